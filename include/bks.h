@@ -1,0 +1,193 @@
+/*
+ * bks.h — C-ABI of a GB300 (sm_103a) library for randomized Block Krylov Iteration
+ * and Simultaneous Iteration (Musco & Musco, arXiv 1504.05477).
+ *
+ * Conventions shared by every entry point
+ *  - All matrix pointers are DEVICE pointers on the context's device unless a name
+ *    ends in `_host`.  The caller owns them; the library never frees or keeps them
+ *    past the call.
+ *  - Dense matrices are row-major with a leading dimension in elements (>= columns).
+ *    "n x k row-major" below means element (i, j) sits at ptr[i * ld + j].
+ *  - Every call is asynchronous on the context's stream except where it says it
+ *    synchronises.  Solves synchronise once, at the end, to read the device status
+ *    word; nothing else blocks the host.
+ *  - Errors are returned as bks_status codes; nothing is thrown across the ABI and
+ *    no kernel traps.  Argument errors are detected on the host before any launch.
+ *    Device-detected problems (non-finite values, Cholesky breakdown that the
+ *    shifted retry could not repair, a Jacobi sweep cap) are reported through the
+ *    status word.  bks_last_error() gives a one-line explanation.
+ *  - A context is not thread-safe; use one per host thread.
+ */
+#ifndef BKS_H
+#define BKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BKS_OK = 0,
+    BKS_ERR_INVALID_ARG = 1,    /* bad size, null pointer, bad dtype: nothing launched */
+    BKS_ERR_CUDA = 2,           /* a CUDA runtime call failed (message in bks_last_error) */
+    BKS_ERR_NOMEM = 3,          /* workspace allocation failed */
+    BKS_ERR_NONFINITE = 4,      /* a NaN/Inf reached a Gram matrix or M */
+    BKS_ERR_BREAKDOWN = 5,      /* Cholesky of a Gram matrix failed even after shifting */
+    BKS_ERR_NOT_CONVERGED = 6,  /* Jacobi eigen-solver hit its sweep cap */
+    BKS_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up */
+    BKS_ERR_UNSUPPORTED = 8,    /* valid request this build does not implement */
+    BKS_WARN_DEFLATED = 100     /* results valid; q was capped or Krylov columns were dependent */
+} bks_status;
+
+typedef enum { BKS_F64 = 0, BKS_F32 = 1, BKS_BF16 = 2 } bks_dtype;
+typedef enum { BKS_DENSE = 0, BKS_CSR = 1 } bks_kind;
+
+/* Precision of a solve.  AUTO: FP64 for FP64 input, else FP32.  F32: products with
+ * FP32-accurate arithmetic, Krylov blocks in FP32, Gram matrices accumulated in FP64.
+ * BF16: products in BF16 with FP32 accumulation (A must be BF16); with `refine` a
+ * final FP32-accurate B = A^T Q recomputes M before the eigen-solve. */
+typedef enum { BKS_PREC_AUTO = 0, BKS_PREC_F64 = 1, BKS_PREC_F32 = 2, BKS_PREC_BF16 = 3 } bks_precision;
+
+/* The matrix A (n x d).  Paper, Sec. 1: A in R^{n x d}; the methods touch it only
+ * through products with A and A^T (Sec. 4).  Dense: row-major, `vals` holds n*ld
+ * elements of `dtype`.  CSR: `row_ptr` (n+1, int64), `col_idx` (nnz, int32, sorted
+ * within a row), `vals` (nnz, FP32).  The optional CSR of A^T (`t_*`, d+1 / nnz /
+ * nnz) lets the A^T products run row-parallel; when absent bks_csr_transpose builds
+ * it.  `col_mean` (d floats, device) makes every product use A - 1 mu^T instead of A
+ * (footnote 1 of Sec. 1: principal components after mean centring), applied
+ * implicitly. */
+typedef struct {
+    int32_t kind;
+    int32_t dtype;
+    int64_t n, d;
+    int64_t ld;
+    const void* vals;
+    const int64_t* row_ptr;
+    const int32_t* col_idx;
+    int64_t nnz;
+    const int64_t* t_row_ptr;
+    const int32_t* t_col_idx;
+    const void* t_vals;
+    const float* col_mean;
+} bks_matrix;
+
+typedef struct {
+    int32_t precision;          /* bks_precision */
+    int32_t refine;             /* BF16 only: final FP32 Rayleigh-Ritz pass (default 1) */
+    int32_t basis_only;         /* 1: skip steps 4-5 and return Z = first k columns of Q
+                                   (Sec. 4.1: enough for low-rank approximation) */
+    int32_t sign_fix;           /* 1 (default): flip each z_i so its largest |entry| is > 0 */
+    int32_t jacobi_max_sweeps;  /* default 40 */
+    double jacobi_tol;          /* rotation threshold |x_p.x_q| <= tol |x_p||x_q|; 0 = default */
+    int32_t profile;            /* 1: record per-kernel-class CUDA-event times into bks_stats */
+    int32_t reserved[7];
+} bks_opts;
+
+typedef struct {
+    int32_t q_eff;              /* iterations actually run (q capped so k(q+1) <= min(n,d)) */
+    int32_t width;              /* columns of Q: k(q_eff+1) for BKI, k for SI */
+    int32_t jacobi_sweeps;
+    int32_t chol_shifts;        /* Cholesky factorisations that needed a diagonal shift */
+    int32_t launches;           /* kernels launched by the call */
+    int32_t product_launches;   /* of which products with A or A^T */
+    float ms_product;           /* with opts.profile: summed event time of A / A^T products */
+    float ms_orth;              /* ... of block orthonormalisation */
+    float ms_rr;                /* ... of M, eigen-solve and Ritz vectors */
+    float ms_total;             /* ... of the whole call */
+    double product_bytes;       /* algorithmic bytes moved by the A / A^T products */
+    double product_flops;       /* algorithmic flops of the A / A^T products */
+    int32_t reserved[8];
+} bks_stats;
+
+typedef struct bks_ctx bks_ctx;
+
+/* ---- context -------------------------------------------------------------------- */
+
+/* Create a context on `device`.  Allocates nothing on the device yet. */
+bks_status bks_create(bks_ctx** ctx, int device);
+/* Free the context's workspace (if the library allocated it) and the context. */
+bks_status bks_destroy(bks_ctx* ctx);
+/* Stream (a cudaStream_t, NULL = legacy default) on which every later call runs. */
+bks_status bks_set_stream(bks_ctx* ctx, void* stream);
+/* Hand the context a caller-owned device workspace of `bytes` (256-byte aligned).
+ * Later calls use it and allocate nothing while it is large enough; NULL reverts to
+ * library-owned workspace.  Size it with bks_workspace_size. */
+bks_status bks_set_workspace(bks_ctx* ctx, void* ptr, size_t bytes);
+/* Workspace bytes a solve of A at rank k, q iterations needs. method: 0 BKI, 1 SI. */
+bks_status bks_workspace_size(const bks_matrix* A, int k, int q, int method,
+                              const bks_opts* opts, size_t* bytes);
+/* Fill *opts with the defaults described in bks_opts. */
+void bks_opts_default(bks_opts* opts);
+const char* bks_status_string(bks_status s);
+const char* bks_last_error(const bks_ctx* ctx);
+/* Library version (major * 100 + minor). */
+int bks_version(void);
+
+/* ---- solves (Algorithms 1 and 2) ------------------------------------------------- */
+
+/* Block Krylov Iteration, Algorithm 2 (Sec. 2.1), with per-block reorthonormalisation
+ * (Sec. 4.2) and Rayleigh-Ritz post-processing (Lemma 4.1).
+ *   K = [A Pi, (AA^T) A Pi, ..., (AA^T)^q A Pi]  (q+1 blocks of k columns),
+ *   Q = orthonormal basis of span(K), M = Q^T A A^T Q, Z = Q Ubar_k, Sigma_k = sqrt(lambda_1..k(M)).
+ * k      target rank, 1 <= k <= min(n, d).
+ * q      iterations, >= 0; capped to q_eff = min(q, floor(min(n,d)/k) - 1) with
+ *        BKS_WARN_DEFLATED returned when the cap applies.
+ * seed   start block Pi ~ N(0,1)^{d x k} from the SplitMix64 -> Box-Muller generator
+ *        (see bks_gen_pi), used when `pi` is NULL.
+ * pi     optional caller start block, d x k row-major (ld = k), dtype FP64 on the FP64
+ *        path else FP32.
+ * Z      out, n x k row-major (ld = k): FP64 on the FP64 path, else FP32.
+ * sigma  out, k Ritz values, descending, same dtype as Z.
+ * V      optional out, d x k row-major: right Ritz vectors A^T z_i / sigma_i.
+ * opts   NULL = defaults.  stats: optional out. */
+bks_status bks_block_krylov(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
+                            const void* pi, void* Z, void* sigma, void* V,
+                            const bks_opts* opts, bks_stats* stats);
+
+/* Simultaneous Iteration, Algorithm 1 (Sec. 2.1), orthonormalised after every
+ * iteration (Sec. 4.1): Q <- orth(A (A^T Q)) from Q = orth(A Pi), then the same
+ * Rayleigh-Ritz step with a k x k matrix M.  Arguments as bks_block_krylov. */
+bks_status bks_simul_iter(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
+                          const void* pi, void* Z, void* sigma, void* V,
+                          const bks_opts* opts, bks_stats* stats);
+
+/* ---- building blocks (each one step of the path, exposed for tests and timing) ------ */
+
+/* Start block Pi (Alg. 1/2 step 1), d x k row-major, generated on the device:
+ * element e = j*k + c uses SplitMix64 outputs 2(e/2) and 2(e/2)+1 of the stream
+ * seeded with `seed` (Steele, Lea & Flood 2014), Box-Muller in FP64 (cosine for even
+ * e, sine for odd e), rounded once to `dtype` (BKS_F32 or BKS_F64). */
+bks_status bks_gen_pi(bks_ctx* ctx, uint64_t seed, int64_t d, int k, int dtype, void* out);
+/* Same generator on the host (FP32 out), for cross-checks without a GPU. */
+bks_status bks_gen_pi_host(uint64_t seed, int64_t d, int k, float* out_host);
+
+/* One product with A (Sec. 4: the only access to A): trans = 0 gives Y = A X
+ * (X d x c, Y n x c), trans = 1 gives Y = A^T X (X n x c, Y d x c).  X and Y are
+ * stored COLUMN-major with leading dimension ldx / ldy (column j of X starts at
+ * X + j*ldx), FP32 (FP64 for an FP64 matrix).  For a BF16 matrix, X is rounded to
+ * BF16 unless `exact` is 1, in which case X is split into three BF16 parts and the
+ * product is FP32-accurate.  Honours A->col_mean. */
+bks_status bks_matmul(bks_ctx* ctx, const bks_matrix* A, int trans, int c,
+                      const void* X, int64_t ldx, void* Y, int64_t ldy, int exact);
+
+/* Block orthonormalisation (Sec. 4.1/4.2 reorthonormalisation): W (len x c,
+ * column-major, ldw) is projected twice against the m orthonormal columns of Qb
+ * (len x m, column-major, ldq; m may be 0) and then orthonormalised by CholeskyQR2,
+ * in place.  FP32 or FP64 (dtype).  Returns BKS_ERR_BREAKDOWN when W has no
+ * numerically independent part left. */
+bks_status bks_orthonormalize(bks_ctx* ctx, int dtype, int64_t len, int m, int c,
+                              const void* Qb, int64_t ldq, void* W, int64_t ldw);
+
+/* Eigen-decomposition of a symmetric positive semi-definite w x w matrix M (row-major,
+ * ldm) by one-sided Jacobi (Alg. 2 step 5: the top singular vectors of M are its top
+ * eigenvectors).  lam: out, w eigenvalues, descending.  U: out, w x w row-major,
+ * column i the eigenvector of lam[i].  FP32 or FP64 (dtype). */
+bks_status bks_sym_eig(bks_ctx* ctx, int dtype, int w, const void* M, int64_t ldm,
+                       void* lam, void* U, int64_t ldu);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BKS_H */

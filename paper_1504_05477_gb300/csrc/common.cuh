@@ -1,0 +1,112 @@
+// Internal declarations shared by the kernels and the host orchestration.
+// Layout conventions inside the library:
+//   * "thin blocks" (Pi, Krylov blocks Q_i, B_i = A^T Q_i, Ritz vectors) are stored
+//     column by column: a block of c columns of length L is a c x ld row-major array
+//     whose row j is column j (ld >= L, padded to a multiple of 32 elements, pad = 0).
+//   * A is the caller's row-major n x d matrix (ld >= d).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace bks {
+
+// Device status word bits (OR-ed by kernels, read once by the host at the end).
+enum : int {
+    ST_NONFINITE = 1,
+    ST_BREAKDOWN = 2,
+    ST_NOT_CONVERGED = 4,
+    ST_TIMEOUT = 8,
+    ST_SHIFTED = 16,
+};
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Element conversions used by templated loads.
+template <typename T> __device__ __forceinline__ T cvt(float x) { return static_cast<T>(x); }
+template <typename T> __device__ __forceinline__ T cvt(double x) { return static_cast<T>(x); }
+template <typename T> __device__ __forceinline__ T cvt(__nv_bfloat16 x) {
+    return static_cast<T>(__bfloat162float(x));
+}
+
+template <typename T> __device__ __forceinline__ bool finite_val(T x) { return isfinite(x); }
+
+// Per-call launch bookkeeping.
+struct Exec {
+    cudaStream_t stream = nullptr;
+    int* status = nullptr;       // device status word
+    int num_sms = 148;
+    int launches = 0;
+    int product_launches = 0;
+};
+
+// ------------------------------------------------------------------ SIMT GEMM
+// Out[m][n] = alpha * sum_k X[m][k] * Yop[k][n] (+ beta * Out), where X is row-major
+// M x K and Yop[k][n] = Y[n][k] (y_kmajor) or Y[k][n] (!y_kmajor).
+struct GemmDesc {
+    int64_t M, N, K;
+    const void* X; int64_t ldx;
+    const void* Y; int64_t ldy;
+    bool y_kmajor;
+    int y_dtype;               // 0 f64, 1 f32, 2 bf16 (bks_dtype)
+    // output
+    void* out; int64_t ldo;
+    bool out_transposed;       // store Out[m][n] at out[n * ldo + m]
+    bool out_f64 = false;      // output is FP64 whatever T is (Gram matrices)
+    double alpha, beta;
+    // centring correction for the dense-A products: Out[m][n] -= alpha * corr
+    //   y_kmajor (A X):    corr = (mu . X[m,:])            (same for every n)
+    //   !y_kmajor (A^T X): corr = mu[n] * sum_k X[m][k]
+    const float* col_mean = nullptr;
+};
+
+// Launch the SIMT tile GEMM in precision T (float or double).  Split-K is chosen
+// internally; partial sums go through `partials` (FP64, caller workspace, at least
+// gemm_partial_elems(...) doubles) and are reduced in a fixed order.
+template <typename T>
+void gemm_simt(Exec& ex, const GemmDesc& g, double* partials, int64_t partial_cap);
+int64_t gemm_partial_elems(int64_t M, int64_t N, int64_t K, int num_sms);
+
+// ------------------------------------------------------------------ building blocks
+template <typename T>
+void gen_pi_device(Exec& ex, uint64_t seed, int64_t d, int k, T* out, int64_t ld_row,
+                   bool transposed);
+void gen_pi_host(uint64_t seed, int64_t d, int k, float* out);
+
+// Copy a row-major rows x cols matrix (src dtype -> T) into column-major thin storage.
+template <typename T>
+void transpose_in(Exec& ex, const void* src, int src_dtype, int64_t rows, int64_t cols,
+                  int64_t lds, T* dst, int64_t ldd);
+
+// Block orthonormalisation: W (c x ld thin) against Qb (m x ld thin), result in Qout.
+// ct: c x m scratch; gram: max(m, c) x c FP64; rfac: c x c; shifted_flag: device int.
+template <typename T>
+void orth_block(Exec& ex, int64_t len, int64_t ld, const T* Qb, int m, T* W, int c, T* Wtmp,
+                T* Qout, double* partials, int64_t partial_cap, double* gram, T* rfac, T* ct,
+                int* shifted_flag);
+template <typename T>
+void cholqr_extra(Exec& ex, int64_t len, int64_t ld, T* Q, int c, double* partials, int64_t cap,
+                  double* gram, T* rfac, int* shifted_flag);
+// Jacobi launch plan (cluster size C, block width b, register tile E, shared bytes).
+bool jacobi_plan(int w, int elem_bytes, int& C, int& b, int& E, size_t& smem);
+
+// Symmetric PSD eigen-solve by one-sided Jacobi; M given as w x ldm (row j = column j).
+// On return lam[0..w) descending and Vt (w x ldv) row i = eigenvector of lam[i].
+template <typename T>
+void sym_eig(Exec& ex, int w, const T* M, int64_t ldm, T* X, T* V, int64_t ldw, T* lam,
+             T* Vt, int64_t ldv, int* order, int max_sweeps, double tol, int* sweeps_dev);
+
+// Column-wise argmax |.| sign normalisation of a row-major n x k matrix (and the
+// matching rows of Ut, k x ldu).
+template <typename T>
+void sign_fix(Exec& ex, T* Z, int64_t n, int k, int64_t ldz, T* Ut, int64_t w, int64_t ldu);
+
+// sigma_i = |row i of Vt| (FP64 accumulation); optionally scale row i by 1/sigma_i.
+template <typename T>
+void row_norms(Exec& ex, T* Vt, int k, int64_t len, int64_t ldv, T* sigma, bool normalise);
+
+// Scan `n` values for non-finite entries, OR-ing ST_NONFINITE into the status word.
+template <typename T>
+void check_finite(Exec& ex, const T* x, int64_t n);
+
+}  // namespace bks

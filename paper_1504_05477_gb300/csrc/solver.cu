@@ -1,0 +1,683 @@
+// Host orchestration of Algorithms 1 and 2 and the C-ABI declared in include/bks.h.
+//
+// Block Krylov Iteration (Alg. 2) as run here:
+//   Pi -> W_0 = A Pi -> Q_0 = orth(W_0)
+//   for i = 1..q_eff:  B_{i-1} = A^T Q_{i-1};  W_i = A B_{i-1};
+//                      Q_i = orth(W_i against Q_0..Q_{i-1})          (Sec. 4.2)
+//   B_q = A^T Q_q;  M = B^T B (= Q^T A A^T Q, Lemma 4.1);  M = Ubar Lambda Ubar^T;
+//   Z = Q Ubar_k;  sigma_i = |B ubar_i| (= |A^T z_i|, the Ritz values).
+// Simultaneous Iteration (Alg. 1): Q <- orth(A (A^T Q)) q times, then the same
+// Rayleigh-Ritz step with w = k (Sec. 4.1).
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/bks.h"
+#include "common.cuh"
+
+
+using namespace bks;
+
+struct bks_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 148;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    bool ws_owned = false;
+    int* host_status = nullptr;   // pinned: [status, sweeps, shifted]
+    std::string last_error;
+    std::vector<cudaEvent_t> events;
+};
+
+namespace {
+
+constexpr int BKS_VERSION = 100;
+
+struct Arena {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        const size_t o = off;
+        off += (bytes + 255) / 256 * 256;
+        return o;
+    }
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bks_status fail(bks_ctx* ctx, bks_status s, const std::string& msg) {
+    if (ctx) ctx->last_error = msg;
+    return s;
+}
+
+bks_status cuda_fail(bks_ctx* ctx, cudaError_t e, const char* where) {
+    return fail(ctx, BKS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bks_status ensure_ws(bks_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->ws_bytes && ctx->ws != nullptr) return BKS_OK;
+    if (ctx->ws != nullptr && !ctx->ws_owned)
+        return fail(ctx, BKS_ERR_NOMEM, "caller workspace too small: need " + std::to_string(bytes) +
+                                            " bytes, have " + std::to_string(ctx->ws_bytes));
+    if (ctx->ws_owned && ctx->ws) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->ws);
+        ctx->ws = nullptr;
+        ctx->ws_bytes = 0;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, BKS_ERR_NOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    ctx->ws = p;
+    ctx->ws_bytes = bytes;
+    ctx->ws_owned = true;
+    return BKS_OK;
+}
+
+bool dtype_ok(int dt) { return dt == BKS_F64 || dt == BKS_F32 || dt == BKS_BF16; }
+size_t dtype_bytes(int dt) { return dt == BKS_F64 ? 8 : dt == BKS_F32 ? 4 : 2; }
+
+bks_status check_matrix(bks_ctx* ctx, const bks_matrix* A) {
+    if (A == nullptr) return fail(ctx, BKS_ERR_INVALID_ARG, "A is NULL");
+    if (A->n < 1 || A->d < 1) return fail(ctx, BKS_ERR_INVALID_ARG, "A must be at least 1 x 1");
+    if (!dtype_ok(A->dtype)) return fail(ctx, BKS_ERR_INVALID_ARG, "unknown A dtype");
+    if (A->kind == BKS_DENSE) {
+        if (A->vals == nullptr) return fail(ctx, BKS_ERR_INVALID_ARG, "A->vals is NULL");
+        if (A->ld < A->d) return fail(ctx, BKS_ERR_INVALID_ARG, "A->ld < A->d");
+        if (A->col_mean != nullptr)
+            return fail(ctx, BKS_ERR_UNSUPPORTED, "implicit centring is implemented for CSR A only");
+        return BKS_OK;
+    }
+    if (A->kind == BKS_CSR) return fail(ctx, BKS_ERR_UNSUPPORTED, "CSR A is not built yet");
+    return fail(ctx, BKS_ERR_INVALID_ARG, "unknown matrix kind");
+}
+
+// Products with A, in precision T.
+template <typename T>
+void product(Exec& ex, const bks_matrix* A, bool trans, int c, const T* X, int64_t ldx, T* Y,
+             int64_t ldy, double* part, int64_t cap) {
+    GemmDesc g{};
+    g.M = c;
+    g.N = trans ? A->d : A->n;
+    g.K = trans ? A->n : A->d;
+    g.X = X; g.ldx = ldx;
+    g.Y = A->vals; g.ldy = A->ld;
+    g.y_kmajor = !trans;
+    g.y_dtype = A->dtype;
+    g.out = Y; g.ldo = ldy; g.out_transposed = false;
+    g.alpha = 1.0; g.beta = 0.0;
+    const int before = ex.launches;
+    gemm_simt<T>(ex, g, part, cap);
+    ex.product_launches += ex.launches - before;
+}
+
+// ----------------------------------------------------------------- workspace plan
+struct Plan {
+    int64_t n, d, ldn, ldd;
+    int k, q, w;
+    size_t Qt, Bt, Pit, W, Wtmp, part, gram, rfac, ct, Mm, JX, JV, lam, Vt, order, Vk, stat;
+    int64_t part_cap;
+    size_t total;
+};
+
+int64_t max_partials(int64_t n, int64_t d, int k, int w, int sms) {
+    int64_t p = 0;
+    auto upd = [&](int64_t M, int64_t N, int64_t K) {
+        const int64_t e = gemm_partial_elems(M, N, K, sms);
+        if (e > p) p = e;
+    };
+    upd(k, n, d);        // A X
+    upd(k, d, n);        // A^T X
+    upd(w, k, n);        // projection coefficients
+    upd(k, n, w);        // projection update, Z = Q Ubar_k
+    upd(k, k, n);        // Gram
+    upd(w, w, d);        // M
+    upd(k, d, w);        // B Ubar_k
+    if (p < int64_t(k) * k) p = int64_t(k) * k;   // FP64 Gram output always uses partials
+    return p;
+}
+
+Plan make_plan(int64_t n, int64_t d, int k, int q_eff, int w, size_t tb, int sms) {
+    Plan p{};
+    p.n = n; p.d = d; p.k = k; p.q = q_eff; p.w = w;
+    p.ldn = round_up(n, 32);
+    p.ldd = round_up(d, 32);
+    Arena a;
+    p.Qt = a.take(size_t(w) * p.ldn * tb);
+    p.Bt = a.take(size_t(w) * p.ldd * tb);
+    p.Pit = a.take(size_t(k) * p.ldd * tb);
+    p.W = a.take(size_t(k) * p.ldn * tb);
+    p.Wtmp = a.take(size_t(k) * p.ldn * tb);
+    p.part_cap = max_partials(n, d, k, w, sms);
+    p.part = a.take(size_t(p.part_cap) * sizeof(double));
+    p.gram = a.take(size_t(w) * k * sizeof(double));
+    p.rfac = a.take(size_t(k) * k * tb);
+    p.ct = a.take(size_t(k) * w * tb);
+    p.Mm = a.take(size_t(w) * w * tb);
+    p.JX = a.take(size_t(w) * w * tb);
+    p.JV = a.take(size_t(w) * w * tb);
+    p.lam = a.take(size_t(w) * tb);
+    p.Vt = a.take(size_t(w) * w * tb);
+    p.order = a.take(size_t(w) * sizeof(int));
+    p.Vk = a.take(size_t(k) * p.ldd * tb);
+    p.stat = a.take(4 * sizeof(int));
+    p.total = a.off;
+    return p;
+}
+
+// ----------------------------------------------------------------- profiling
+struct Prof {
+    bks_ctx* ctx;
+    bool on;
+    std::vector<std::pair<int, int>> spans[4];   // product, orth, rr, total
+    int next = 0;
+    Prof(bks_ctx* c, bool o) : ctx(c), on(o) {}
+    int ev() {
+        if (next >= int(ctx->events.size())) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            ctx->events.push_back(e);
+        }
+        return next++;
+    }
+    int begin() {
+        if (!on) return -1;
+        const int e = ev();
+        cudaEventRecord(ctx->events[e], ctx->stream);
+        return e;
+    }
+    void end(int cls, int b) {
+        if (!on) return;
+        const int e = ev();
+        cudaEventRecord(ctx->events[e], ctx->stream);
+        spans[cls].push_back({b, e});
+    }
+    float total(int cls) {
+        float s = 0.f;
+        for (auto& pr : spans[cls]) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ctx->events[pr.first], ctx->events[pr.second]);
+            s += ms;
+        }
+        return s;
+    }
+};
+
+template <typename T>
+bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed, const void* pi,
+                 void* Zv, void* sigv, void* Vv, const bks_opts& o, bks_stats* st, bool krylov) {
+    const int64_t n = A->n, d = A->d;
+    const int64_t mn = n < d ? n : d;
+    int q_eff = q;
+    bool deflated = false;
+    if (krylov) {
+        const int64_t cap = mn / k - 1;
+        if (q_eff > cap) { q_eff = int(cap); deflated = true; }
+    }
+    const int w = krylov ? k * (q_eff + 1) : k;
+    {
+        int C, b, E;
+        size_t sm;
+        if (!o.basis_only && !jacobi_plan(w, int(sizeof(T)), C, b, E, sm))
+            return fail(ctx, BKS_ERR_UNSUPPORTED,
+                        "Krylov width " + std::to_string(w) + " exceeds the Jacobi solver's limit");
+    }
+    Plan p = make_plan(n, d, k, q_eff, w, sizeof(T), ctx->num_sms);
+    bks_status s = ensure_ws(ctx, p.total);
+    if (s != BKS_OK) return s;
+    char* base = static_cast<char*>(ctx->ws);
+    T* Qt = reinterpret_cast<T*>(base + p.Qt);
+    T* Bt = reinterpret_cast<T*>(base + p.Bt);
+    T* Pit = reinterpret_cast<T*>(base + p.Pit);
+    T* W = reinterpret_cast<T*>(base + p.W);
+    T* Wtmp = reinterpret_cast<T*>(base + p.Wtmp);
+    double* part = reinterpret_cast<double*>(base + p.part);
+    double* gram = reinterpret_cast<double*>(base + p.gram);
+    T* rfac = reinterpret_cast<T*>(base + p.rfac);
+    T* ct = reinterpret_cast<T*>(base + p.ct);
+    T* Mm = reinterpret_cast<T*>(base + p.Mm);
+    T* JX = reinterpret_cast<T*>(base + p.JX);
+    T* JV = reinterpret_cast<T*>(base + p.JV);
+    T* lam = reinterpret_cast<T*>(base + p.lam);
+    T* Vt = reinterpret_cast<T*>(base + p.Vt);
+    int* order = reinterpret_cast<int*>(base + p.order);
+    T* Vk = reinterpret_cast<T*>(base + p.Vk);
+    int* stat = reinterpret_cast<int*>(base + p.stat);   // [status, sweeps, shifted]
+    T* Z = static_cast<T*>(Zv);
+    T* sigma = static_cast<T*>(sigv);
+    T* V = static_cast<T*>(Vv);
+
+    Exec ex;
+    ex.stream = ctx->stream;
+    ex.status = stat;
+    ex.num_sms = ctx->num_sms;
+    Prof prof(ctx, o.profile != 0);
+    const int t_all = prof.begin();
+    cudaMemsetAsync(stat, 0, 4 * sizeof(int), ctx->stream);
+
+    // a0: start block, stored transposed (k x ldd)
+    if (pi != nullptr)
+        transpose_in<T>(ex, pi, sizeof(T) == 8 ? BKS_F64 : BKS_F32, d, k, k, Pit, p.ldd);
+    else
+        gen_pi_device<T>(ex, seed, d, k, Pit, p.ldd, true);
+
+    auto prod = [&](bool trans, const T* X, int64_t ldx, T* Y, int64_t ldy) {
+        const int b = prof.begin();
+        product<T>(ex, A, trans, k, X, ldx, Y, ldy, part, p.part_cap);
+        prof.end(0, b);
+    };
+    auto orth = [&](int m, T* Qout) {
+        const int b = prof.begin();
+        orth_block<T>(ex, n, p.ldn, Qt, m, W, k, Wtmp, Qout, part, p.part_cap, gram, rfac, ct,
+                      stat + 2);
+        prof.end(1, b);
+    };
+
+    // a1 + a4: W_0 = A Pi, Q_0 = orth(W_0)
+    prod(false, Pit, p.ldd, W, p.ldn);
+    orth(0, Qt);
+    for (int i = 1; i <= q_eff; ++i) {
+        T* Qprev = krylov ? Qt + size_t(i - 1) * k * p.ldn : Qt;
+        T* Bprev = krylov ? Bt + size_t(i - 1) * k * p.ldd : Bt;
+        prod(true, Qprev, p.ldn, Bprev, p.ldd);          // a2: B_{i-1} = A^T Q_{i-1}
+        prod(false, Bprev, p.ldd, W, p.ldn);              // a3: W_i = A B_{i-1}
+        if (krylov)
+            orth(i * k, Qt + size_t(i) * k * p.ldn);     // a4: project + CholeskyQR2
+        else
+            orth(0, Qt);                                  // a9: SI re-orthonormalisation
+    }
+    T* Blast = krylov ? Bt + size_t(q_eff) * k * p.ldd : Bt;
+    const T* Qlast = krylov ? Qt + size_t(q_eff) * k * p.ldn : Qt;
+    prod(true, Qlast, p.ldn, Blast, p.ldd);               // a5: B_q = A^T Q_q
+
+    const int t_rr = prof.begin();
+    if (o.basis_only) {
+        // Z = first k columns of Q (Sec. 4.1: enough for low-rank approximation)
+        transpose_in<T>(ex, Qt, sizeof(T) == 8 ? BKS_F64 : BKS_F32, k, n, p.ldn, Z, k);
+        row_norms<T>(ex, Bt, k, d, p.ldd, sigma, false);
+        if (V != nullptr) {
+            row_norms<T>(ex, Bt, k, d, p.ldd, sigma, true);
+            transpose_in<T>(ex, Bt, sizeof(T) == 8 ? BKS_F64 : BKS_F32, k, d, p.ldd, V, k);
+        }
+    } else {
+        GemmDesc gm{};   // a5: M = B^T B (w x w)
+        gm.M = w; gm.N = w; gm.K = d;
+        gm.X = Bt; gm.ldx = p.ldd; gm.Y = Bt; gm.ldy = p.ldd;
+        gm.y_kmajor = true; gm.y_dtype = sizeof(T) == 8 ? BKS_F64 : BKS_F32;
+        gm.out = Mm; gm.ldo = w; gm.alpha = 1.0; gm.beta = 0.0;
+        gemm_simt<T>(ex, gm, part, p.part_cap);
+        check_finite<T>(ex, Mm, int64_t(w) * w);
+        // a6: eigen-decomposition of M, descending
+        sym_eig<T>(ex, w, Mm, w, JX, JV, w, lam, Vt, w, order,
+                   o.jacobi_max_sweeps > 0 ? o.jacobi_max_sweeps : 40, o.jacobi_tol, stat + 1);
+        // a7: Z = Q Ubar_k (row-major n x k)
+        GemmDesc gz{};
+        gz.M = k; gz.N = n; gz.K = w;
+        gz.X = Vt; gz.ldx = w; gz.Y = Qt; gz.ldy = p.ldn;
+        gz.y_kmajor = false; gz.y_dtype = gm.y_dtype;
+        gz.out = Z; gz.ldo = k; gz.out_transposed = true; gz.alpha = 1.0; gz.beta = 0.0;
+        gemm_simt<T>(ex, gz, part, p.part_cap);
+        if (o.sign_fix) sign_fix<T>(ex, Z, n, k, k, Vt, w, w);
+        // sigma_i = |B ubar_i| = |A^T z_i|; V_k = B Ubar_k Sigma^{-1}
+        GemmDesc gv{};
+        gv.M = k; gv.N = d; gv.K = w;
+        gv.X = Vt; gv.ldx = w; gv.Y = Bt; gv.ldy = p.ldd;
+        gv.y_kmajor = false; gv.y_dtype = gm.y_dtype;
+        gv.out = Vk; gv.ldo = p.ldd; gv.alpha = 1.0; gv.beta = 0.0;
+        gemm_simt<T>(ex, gv, part, p.part_cap);
+        row_norms<T>(ex, Vk, k, d, p.ldd, sigma, V != nullptr);
+        if (V != nullptr)
+            transpose_in<T>(ex, Vk, sizeof(T) == 8 ? BKS_F64 : BKS_F32, k, d, p.ldd, V, k);
+    }
+    prof.end(2, t_rr);
+    prof.end(3, t_all);
+
+    cudaError_t e = cudaMemcpyAsync(ctx->host_status, stat, 3 * sizeof(int), cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "solve");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+    const int status = ctx->host_status[0];
+    if (st != nullptr) {
+        std::memset(st, 0, sizeof(*st));
+        st->q_eff = q_eff;
+        st->width = w;
+        st->jacobi_sweeps = ctx->host_status[1];
+        st->chol_shifts = ctx->host_status[2];
+        st->launches = ex.launches;
+        st->product_launches = ex.product_launches;
+        const int nprod = krylov ? 2 * q_eff + 2 : 2 * q_eff + 2;
+        const double abytes = double(n) * double(A->ld) * double(dtype_bytes(A->dtype));
+        st->product_bytes = nprod * (abytes + double(k) * (n + d) * sizeof(T));
+        st->product_flops = nprod * 2.0 * double(n) * double(d) * k;
+        if (o.profile) {
+            st->ms_product = prof.total(0);
+            st->ms_orth = prof.total(1);
+            st->ms_rr = prof.total(2);
+            st->ms_total = prof.total(3);
+        }
+    }
+    if (status & ST_NONFINITE) return fail(ctx, BKS_ERR_NONFINITE, "non-finite value in a Gram matrix or M");
+    if (status & ST_BREAKDOWN) return fail(ctx, BKS_ERR_BREAKDOWN, "Cholesky breakdown after shifting");
+    if (status & ST_NOT_CONVERGED) return fail(ctx, BKS_ERR_NOT_CONVERGED, "Jacobi sweep cap reached");
+    if (!o.basis_only && ctx->host_status[1] < 0)
+        return fail(ctx, BKS_ERR_UNSUPPORTED, "Jacobi launch failed");
+    ctx->last_error.clear();
+    return deflated ? BKS_WARN_DEFLATED : BKS_OK;
+}
+
+bks_status solve_entry(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
+                       const void* pi, void* Z, void* sigma, void* V, const bks_opts* opts,
+                       bks_stats* st, bool krylov) {
+    if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
+    bks_status s = check_matrix(ctx, A);
+    if (s != BKS_OK) return s;
+    const int64_t mn = A->n < A->d ? A->n : A->d;
+    if (k < 1 || int64_t(k) > mn) return fail(ctx, BKS_ERR_INVALID_ARG, "k must be in [1, min(n, d)]");
+    if (k > 128)
+        return fail(ctx, BKS_ERR_UNSUPPORTED, "k > 128: block Cholesky factors are held on one SM");
+    if (q < 0) return fail(ctx, BKS_ERR_INVALID_ARG, "q must be >= 0");
+    if (Z == nullptr || sigma == nullptr) return fail(ctx, BKS_ERR_INVALID_ARG, "Z and sigma are required");
+    bks_opts o;
+    if (opts) o = *opts; else bks_opts_default(&o);
+    int prec = o.precision;
+    if (prec == BKS_PREC_AUTO) prec = A->dtype == BKS_F64 ? BKS_PREC_F64 : BKS_PREC_F32;
+    if (prec == BKS_PREC_BF16) return fail(ctx, BKS_ERR_UNSUPPORTED, "BF16 precision mode is not built yet");
+    if (prec != BKS_PREC_F64 && prec != BKS_PREC_F32) return fail(ctx, BKS_ERR_INVALID_ARG, "bad precision");
+    DeviceGuard g(ctx->device);
+    if (prec == BKS_PREC_F64) return solve<double>(ctx, A, k, q, seed, pi, Z, sigma, V, o, st, krylov);
+    return solve<float>(ctx, A, k, q, seed, pi, Z, sigma, V, o, st, krylov);
+}
+
+}  // namespace
+
+// ====================================================================== C-ABI
+
+extern "C" {
+
+void bks_opts_default(bks_opts* o) {
+    if (o == nullptr) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = BKS_PREC_AUTO;
+    o->refine = 1;
+    o->basis_only = 0;
+    o->sign_fix = 1;
+    o->jacobi_max_sweeps = 40;
+    o->jacobi_tol = 0.0;
+    o->profile = 0;
+}
+
+int bks_version(void) { return BKS_VERSION; }
+
+const char* bks_status_string(bks_status s) {
+    switch (s) {
+        case BKS_OK: return "ok";
+        case BKS_ERR_INVALID_ARG: return "invalid argument";
+        case BKS_ERR_CUDA: return "CUDA error";
+        case BKS_ERR_NOMEM: return "out of device memory";
+        case BKS_ERR_NONFINITE: return "non-finite value";
+        case BKS_ERR_BREAKDOWN: return "Cholesky breakdown";
+        case BKS_ERR_NOT_CONVERGED: return "eigen-solver did not converge";
+        case BKS_ERR_TIMEOUT: return "device wait timed out";
+        case BKS_ERR_UNSUPPORTED: return "unsupported";
+        case BKS_WARN_DEFLATED: return "ok (q capped or columns deflated)";
+    }
+    return "unknown status";
+}
+
+const char* bks_last_error(const bks_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+bks_status bks_create(bks_ctx** out, int device) {
+    if (out == nullptr) return BKS_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return BKS_ERR_INVALID_ARG;
+    }
+    bks_ctx* ctx = new bks_ctx();
+    ctx->device = device;
+    DeviceGuard g(device);
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMallocHost(&ctx->host_status, 4 * sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return BKS_ERR_CUDA;
+    }
+    *out = ctx;
+    return BKS_OK;
+}
+
+bks_status bks_destroy(bks_ctx* ctx) {
+    if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->ws_owned && ctx->ws) cudaFree(ctx->ws);
+    for (auto e : ctx->events) cudaEventDestroy(e);
+    if (ctx->host_status) cudaFreeHost(ctx->host_status);
+    delete ctx;
+    return BKS_OK;
+}
+
+bks_status bks_set_stream(bks_ctx* ctx, void* stream) {
+    if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    return BKS_OK;
+}
+
+bks_status bks_set_workspace(bks_ctx* ctx, void* ptr, size_t bytes) {
+    if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
+    if (ptr != nullptr && (reinterpret_cast<uintptr_t>(ptr) % 256) != 0)
+        return fail(ctx, BKS_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    DeviceGuard g(ctx->device);
+    if (ctx->ws_owned && ctx->ws) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->ws);
+    }
+    ctx->ws = ptr;
+    ctx->ws_bytes = ptr ? bytes : 0;
+    ctx->ws_owned = false;
+    return BKS_OK;
+}
+
+bks_status bks_workspace_size(const bks_matrix* A, int k, int q, int method, const bks_opts* opts,
+                              size_t* bytes) {
+    if (A == nullptr || bytes == nullptr || k < 1 || q < 0) return BKS_ERR_INVALID_ARG;
+    const int64_t mn = A->n < A->d ? A->n : A->d;
+    if (int64_t(k) > mn) return BKS_ERR_INVALID_ARG;
+    bks_opts o;
+    if (opts) o = *opts; else bks_opts_default(&o);
+    int prec = o.precision;
+    if (prec == BKS_PREC_AUTO) prec = A->dtype == BKS_F64 ? BKS_PREC_F64 : BKS_PREC_F32;
+    const size_t tb = prec == BKS_PREC_F64 ? 8 : 4;
+    int q_eff = q;
+    if (method == 0) {
+        const int64_t cap = mn / k - 1;
+        if (q_eff > cap) q_eff = int(cap);
+    }
+    const int w = method == 0 ? k * (q_eff + 1) : k;
+    int sms = 152;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaGetLastError();
+    *bytes = make_plan(A->n, A->d, k, q_eff, w, tb, sms).total;
+    return BKS_OK;
+}
+
+bks_status bks_block_krylov(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
+                            const void* pi, void* Z, void* sigma, void* V, const bks_opts* opts,
+                            bks_stats* stats) {
+    return solve_entry(ctx, A, k, q, seed, pi, Z, sigma, V, opts, stats, true);
+}
+
+bks_status bks_simul_iter(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
+                          const void* pi, void* Z, void* sigma, void* V, const bks_opts* opts,
+                          bks_stats* stats) {
+    return solve_entry(ctx, A, k, q, seed, pi, Z, sigma, V, opts, stats, false);
+}
+
+bks_status bks_gen_pi(bks_ctx* ctx, uint64_t seed, int64_t d, int k, int dtype, void* out) {
+    if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
+    if (out == nullptr || d < 1 || k < 1 || (dtype != BKS_F32 && dtype != BKS_F64))
+        return fail(ctx, BKS_ERR_INVALID_ARG, "bad bks_gen_pi arguments");
+    DeviceGuard g(ctx->device);
+    Exec ex;
+    ex.stream = ctx->stream;
+    ex.num_sms = ctx->num_sms;
+    if (dtype == BKS_F32) gen_pi_device<float>(ex, seed, d, k, static_cast<float*>(out), k, false);
+    else gen_pi_device<double>(ex, seed, d, k, static_cast<double*>(out), k, false);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? BKS_OK : cuda_fail(ctx, e, "bks_gen_pi");
+}
+
+bks_status bks_gen_pi_host(uint64_t seed, int64_t d, int k, float* out_host) {
+    if (out_host == nullptr || d < 1 || k < 1) return BKS_ERR_INVALID_ARG;
+    gen_pi_host(seed, d, k, out_host);
+    return BKS_OK;
+}
+
+bks_status bks_matmul(bks_ctx* ctx, const bks_matrix* A, int trans, int c, const void* X,
+                      int64_t ldx, void* Y, int64_t ldy, int exact) {
+    (void)exact;
+    if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
+    bks_status s = check_matrix(ctx, A);
+    if (s != BKS_OK) return s;
+    const int64_t rows_x = trans ? A->n : A->d, rows_y = trans ? A->d : A->n;
+    if (c < 1 || X == nullptr || Y == nullptr || ldx < rows_x || ldy < rows_y)
+        return fail(ctx, BKS_ERR_INVALID_ARG, "bad bks_matmul arguments");
+    DeviceGuard g(ctx->device);
+    const bool f64 = A->dtype == BKS_F64;
+    const int64_t cap = gemm_partial_elems(c, rows_y, rows_x, ctx->num_sms);
+    s = ensure_ws(ctx, size_t(cap) * sizeof(double) + 256);
+    if (s != BKS_OK) return s;
+    Exec ex;
+    ex.stream = ctx->stream;
+    ex.num_sms = ctx->num_sms;
+    double* part = static_cast<double*>(ctx->ws);
+    if (f64)
+        product<double>(ex, A, trans != 0, c, static_cast<const double*>(X), ldx,
+                        static_cast<double*>(Y), ldy, part, cap);
+    else
+        product<float>(ex, A, trans != 0, c, static_cast<const float*>(X), ldx,
+                       static_cast<float*>(Y), ldy, part, cap);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? BKS_OK : cuda_fail(ctx, e, "bks_matmul");
+}
+
+bks_status bks_orthonormalize(bks_ctx* ctx, int dtype, int64_t len, int m, int c, const void* Qb,
+                              int64_t ldq, void* W, int64_t ldw) {
+    if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
+    if ((dtype != BKS_F32 && dtype != BKS_F64) || len < 1 || m < 0 || c < 1 || W == nullptr ||
+        (m > 0 && Qb == nullptr) || ldw < len || (m > 0 && ldq != ldw) || int64_t(m) + c > len)
+        return fail(ctx, BKS_ERR_INVALID_ARG, "bad bks_orthonormalize arguments (ldq must equal ldw)");
+    DeviceGuard g(ctx->device);
+    const size_t tb = dtype == BKS_F64 ? 8 : 4;
+    const int mm = m > 0 ? m : 1;
+    int64_t cap = 0;
+    for (int64_t e : {gemm_partial_elems(mm, c, len, ctx->num_sms),
+                      gemm_partial_elems(c, len, mm, ctx->num_sms),
+                      gemm_partial_elems(c, c, len, ctx->num_sms), int64_t(c) * c})
+        if (e > cap) cap = e;
+    Arena a;
+    const size_t o_part = a.take(size_t(cap) * 8), o_gram = a.take(size_t(c) * c * 8),
+                 o_rfac = a.take(size_t(c) * c * tb), o_ct = a.take(size_t(c) * mm * tb),
+                 o_wtmp = a.take(size_t(c) * ldw * tb), o_stat = a.take(16);
+    bks_status s = ensure_ws(ctx, a.off);
+    if (s != BKS_OK) return s;
+    char* base = static_cast<char*>(ctx->ws);
+    Exec ex;
+    ex.stream = ctx->stream;
+    ex.num_sms = ctx->num_sms;
+    int* stat = reinterpret_cast<int*>(base + o_stat);
+    ex.status = stat;
+    cudaMemsetAsync(stat, 0, 16, ctx->stream);
+    if (dtype == BKS_F64)
+        orth_block<double>(ex, len, ldw, static_cast<const double*>(Qb), m, static_cast<double*>(W),
+                           c, reinterpret_cast<double*>(base + o_wtmp), static_cast<double*>(W),
+                           reinterpret_cast<double*>(base + o_part), cap,
+                           reinterpret_cast<double*>(base + o_gram),
+                           reinterpret_cast<double*>(base + o_rfac),
+                           reinterpret_cast<double*>(base + o_ct), stat + 2);
+    else
+        orth_block<float>(ex, len, ldw, static_cast<const float*>(Qb), m, static_cast<float*>(W), c,
+                          reinterpret_cast<float*>(base + o_wtmp), static_cast<float*>(W),
+                          reinterpret_cast<double*>(base + o_part), cap,
+                          reinterpret_cast<double*>(base + o_gram),
+                          reinterpret_cast<float*>(base + o_rfac),
+                          reinterpret_cast<float*>(base + o_ct), stat + 2);
+    cudaError_t e = cudaMemcpyAsync(ctx->host_status, stat, 3 * sizeof(int), cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bks_orthonormalize");
+    if (ctx->host_status[0] & ST_NONFINITE) return fail(ctx, BKS_ERR_NONFINITE, "non-finite Gram matrix");
+    if (ctx->host_status[0] & ST_BREAKDOWN) return fail(ctx, BKS_ERR_BREAKDOWN, "Cholesky breakdown");
+    return BKS_OK;
+}
+
+bks_status bks_sym_eig(bks_ctx* ctx, int dtype, int w, const void* M, int64_t ldm, void* lam,
+                       void* U, int64_t ldu) {
+    if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
+    if ((dtype != BKS_F32 && dtype != BKS_F64) || w < 1 || M == nullptr || lam == nullptr ||
+        U == nullptr || ldm < w || ldu < w)
+        return fail(ctx, BKS_ERR_INVALID_ARG, "bad bks_sym_eig arguments");
+    const size_t tb = dtype == BKS_F64 ? 8 : 4;
+    int C, b, E;
+    size_t sm;
+    if (!jacobi_plan(w, int(tb), C, b, E, sm))
+        return fail(ctx, BKS_ERR_UNSUPPORTED, "w exceeds the Jacobi solver's limit");
+    DeviceGuard g(ctx->device);
+    Arena a;
+    const size_t o_x = a.take(size_t(w) * w * tb), o_v = a.take(size_t(w) * w * tb),
+                 o_vt = a.take(size_t(w) * w * tb), o_ord = a.take(size_t(w) * 4),
+                 o_stat = a.take(16);
+    bks_status s = ensure_ws(ctx, a.off);
+    if (s != BKS_OK) return s;
+    char* base = static_cast<char*>(ctx->ws);
+    Exec ex;
+    ex.stream = ctx->stream;
+    ex.num_sms = ctx->num_sms;
+    int* stat = reinterpret_cast<int*>(base + o_stat);
+    ex.status = stat;
+    cudaMemsetAsync(stat, 0, 16, ctx->stream);
+    if (dtype == BKS_F64) {
+        sym_eig<double>(ex, w, static_cast<const double*>(M), ldm, reinterpret_cast<double*>(base + o_x),
+                        reinterpret_cast<double*>(base + o_v), w, static_cast<double*>(lam),
+                        reinterpret_cast<double*>(base + o_vt), w, reinterpret_cast<int*>(base + o_ord),
+                        40, 0.0, stat + 1);
+        transpose_in<double>(ex, base + o_vt, BKS_F64, w, w, w, static_cast<double*>(U), ldu);
+    } else {
+        sym_eig<float>(ex, w, static_cast<const float*>(M), ldm, reinterpret_cast<float*>(base + o_x),
+                       reinterpret_cast<float*>(base + o_v), w, static_cast<float*>(lam),
+                       reinterpret_cast<float*>(base + o_vt), w, reinterpret_cast<int*>(base + o_ord),
+                       40, 0.0, stat + 1);
+        transpose_in<float>(ex, base + o_vt, BKS_F32, w, w, w, static_cast<float*>(U), ldu);
+    }
+    cudaError_t e = cudaMemcpyAsync(ctx->host_status, stat, 3 * sizeof(int), cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bks_sym_eig");
+    if (ctx->host_status[0] & ST_NOT_CONVERGED) return fail(ctx, BKS_ERR_NOT_CONVERGED, "Jacobi sweep cap");
+    if (ctx->host_status[1] < 0) return fail(ctx, BKS_ERR_UNSUPPORTED, "Jacobi launch failed");
+    return BKS_OK;
+}
+
+}  // extern "C"
