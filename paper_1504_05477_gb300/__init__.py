@@ -156,13 +156,21 @@ def simul_iter(a, k, q, seed=0, pi=None, want_v=False, precision="auto", stats=F
     return _solve("bks_simul_iter", a, k, q, seed, pi, want_v, precision, stats, **kw)
 
 
+def _colmajor(x):
+    """Column-major copy of a (rows x c) tensor as a (c x rows) array with row stride
+    `rows` (torch keeps stride 1 on size-1 dimensions, so .contiguous() is not enough)."""
+    out = _torch().empty((x.shape[1], x.shape[0]), dtype=x.dtype, device=x.device)
+    out.copy_(x.t())
+    return out
+
+
 def matmul(a, x, trans=False):
     """Y = A X (trans False) or Y = A^T X (trans True) through bks_matmul.  x is a
     (rows x c) CUDA tensor; the result is (rows' x c) in x's dtype."""
     torch = _torch()
     mat = dense_matrix(a)
     ctx = context(a.device)
-    xt = x.t().contiguous()                    # column-major X
+    xt = _colmajor(x)
     rows_y = mat.d if trans else mat.n
     yt = torch.empty((x.shape[1], rows_y), dtype=x.dtype, device=x.device)
     B.check(ctx.lib.bks_matmul(ctx.ptr, ctypes.byref(mat), int(trans), x.shape[1],
@@ -178,10 +186,10 @@ def orthonormalize(w, qb=None):
     torch = _torch()
     ctx = context(w.device)
     code = _dtype_code(w.dtype)
-    wt = w.t().contiguous()
+    wt = _colmajor(w)
     m = 0 if qb is None else qb.shape[1]
     if m:
-        qt = qb.t().contiguous()
+        qt = _colmajor(qb)
         if qt.stride(0) != wt.stride(0):
             raise ValueError("Qb and W must have the same length")
         qptr = ctypes.c_void_p(qt.data_ptr())

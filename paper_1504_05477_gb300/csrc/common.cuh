@@ -90,10 +90,11 @@ void cholqr_extra(Exec& ex, int64_t len, int64_t ld, T* Q, int c, double* partia
 // Jacobi launch plan (cluster size C, block width b, register tile E, shared bytes).
 bool jacobi_plan(int w, int elem_bytes, int& C, int& b, int& E, size_t& smem);
 
-// Symmetric PSD eigen-solve by one-sided Jacobi; M given as w x ldm (row j = column j).
-// On return lam[0..w) descending and Vt (w x ldv) row i = eigenvector of lam[i].
+// One-sided Jacobi on X (w x w, column j = row j of Xin; X is a w x ldw scratch copy).
+// On return lam[0..w) = column norms of the converged X (descending), nrm[j] the norm
+// of column j, Vt (w x ldv) row i = normalised column of lam[i].
 template <typename T>
-void sym_eig(Exec& ex, int w, const T* M, int64_t ldm, T* X, T* V, int64_t ldw, T* lam,
+void sym_eig(Exec& ex, int w, const T* Xin, int64_t ldx, T* X, int64_t ldw, T* lam, T* nrm,
              T* Vt, int64_t ldv, int* order, int max_sweeps, double tol, int* sweeps_dev);
 
 // Column-wise argmax |.| sign normalisation of a row-major n x k matrix (and the

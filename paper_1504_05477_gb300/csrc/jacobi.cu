@@ -46,7 +46,7 @@ __device__ __forceinline__ bool rot_coeffs(T alpha, T beta, T gamma, T tol, T& c
 
 // Both columns in shared memory (intra-block pairs).
 template <typename T, int E>
-__device__ bool rotate_smem_pair(T* xp, T* xq, T* vp, T* vq, T tol, int lane) {
+__device__ bool rotate_smem_pair(T* xp, T* xq, T tol, int lane) {
     T a = 0, b = 0, g = 0;
     T p[E], q[E];
 #pragma unroll
@@ -65,12 +65,6 @@ __device__ bool rotate_smem_pair(T* xp, T* xq, T* vp, T* vq, T tol, int lane) {
         xp[lane + 32 * e] = c * p[e] - s * q[e];
         xq[lane + 32 * e] = s * p[e] + c * q[e];
     }
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const T pv = vp[lane + 32 * e], qv = vq[lane + 32 * e];
-        vp[lane + 32 * e] = c * pv - s * qv;
-        vq[lane + 32 * e] = s * pv + c * qv;
-    }
     return true;
 }
 
@@ -85,11 +79,14 @@ __device__ __forceinline__ void circle_pair(int P, int s, int i, int& a, int& b)
     }
 }
 
-// Shared-memory layout per CTA: [slot 0..1][col 0..b)[X | V][wp].
+constexpr int MOVE_REGS = 16;   // registers per thread per slot used to move one chunk
+
+// One-sided Jacobi on the columns of X (w x w; column j is row j of the input array).
+// Shared-memory layout per CTA: [slot 0..1][col 0..b)[WP].
 template <typename T, int E>
 __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
-    const T* __restrict__ M, int64_t ldm, int w, int b, T* Xout, T* Vout, int64_t ldw,
-    int max_sweeps, T tol, int* status, int* sweeps_out) {
+    const T* __restrict__ Xin, int64_t ldx, int w, int b, T* Xout, int64_t ldw, int max_sweeps,
+    T tol, int* status, int* sweeps_out) {
     constexpr int WP = 32 * E;
     extern __shared__ unsigned char smem_raw[];
     T* buf = reinterpret_cast<T*>(smem_raw);
@@ -101,9 +98,7 @@ __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
     const int C = int(cluster.num_blocks());
     const int rank = int(cluster.block_rank());
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    auto col = [&](int slot, int j, int which) -> T* {
-        return buf + ((size_t(slot) * b + j) * 2 + which) * WP;
-    };
+    auto col = [&](int slot, int j) -> T* { return buf + (size_t(slot) * b + j) * WP; };
 
     // initial placement: CTA r holds blocks 2r (slot 0) and 2r+1 (slot 1)
     if (tid == 0) {
@@ -114,21 +109,19 @@ __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
         const int blk = 2 * rank + slot;
         for (int j = 0; j < b; ++j) {
             const int gc = blk * b + j;
-            T* x = col(slot, j, 0);
-            T* v = col(slot, j, 1);
-            for (int l = tid; l < WP; l += blockDim.x) {
-                const bool live = gc < w && l < w;
-                x[l] = live ? M[int64_t(gc) * ldm + l] : T(0);
-                v[l] = (gc < w && l == gc) ? T(1) : T(0);
-            }
+            T* x = col(slot, j);
+            for (int l = tid; l < WP; l += blockDim.x)
+                x[l] = (gc < w && l < w) ? Xin[int64_t(gc) * ldx + l] : T(0);
         }
     }
     if (tid < 32) flags[tid >> 4][tid & 15] = 0;
     __syncthreads();
     cluster.sync();
 
-    const int P = 2 * C;               // players in the round robin
+    const int P = 2 * C;               // players in the block round robin
     const int bp = b + (b & 1);        // intra-block players (even)
+    const int per_slot = b * WP;
+    const int chunk = JW * 32 * MOVE_REGS;
     int sweep = 0;
     bool converged = false;
     for (; sweep < max_sweeps && !converged; ++sweep) {
@@ -137,37 +130,30 @@ __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
         bool any = false;
         for (int round = 0; round < P - 1; ++round) {
             if (round == 0) {
-                // intra-block pairs of both slots
+                // intra-block pairs of both slots, once per sweep
                 for (int s = 0; s < bp - 1; ++s) {
                     for (int u = warp; u < bp; u += JW) {
                         const int slot = u / (bp / 2), i = u % (bp / 2);
                         int a, c2;
                         circle_pair(bp, s, i, a, c2);
                         if (a >= b || c2 >= b) continue;
-                        any |= rotate_smem_pair<T, E>(col(slot, a, 0), col(slot, c2, 0),
-                                                      col(slot, a, 1), col(slot, c2, 1), tol,
-                                                      lane);
+                        any |= rotate_smem_pair<T, E>(col(slot, a), col(slot, c2), tol, lane);
                     }
                     __syncthreads();
                 }
             }
-            // cross pairs: warp j keeps slot-0 column j in registers
+            // cross pairs: warp keeps slot-0 column j in registers for b sub-rounds
             for (int j0 = 0; j0 < b; j0 += JW) {
                 const int j = j0 + warp;
                 const bool own = j < b;
-                T xr[E], vr[E];
+                T xr[E];
                 if (own) {
 #pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        xr[e] = col(0, j, 0)[lane + 32 * e];
-                        vr[e] = col(0, j, 1)[lane + 32 * e];
-                    }
+                    for (int e = 0; e < E; ++e) xr[e] = col(0, j)[lane + 32 * e];
                 }
                 for (int s = 0; s < b; ++s) {
                     if (own) {
-                        const int qj = (j + s) % b;
-                        T* xq = col(1, qj, 0);
-                        T* vq = col(1, qj, 1);
+                        T* xq = col(1, (j + s) % b);
                         T q[E];
                         T a = 0, bb = 0, g = 0;
 #pragma unroll
@@ -187,59 +173,50 @@ __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
                                 xr[e] = c * p - sn * q[e];
                                 xq[lane + 32 * e] = sn * p + c * q[e];
                             }
-#pragma unroll
-                            for (int e = 0; e < E; ++e) {
-                                const T pv = vr[e], qv = vq[lane + 32 * e];
-                                vr[e] = c * pv - sn * qv;
-                                vq[lane + 32 * e] = sn * pv + c * qv;
-                            }
                         }
                     }
                     __syncthreads();
                 }
                 if (own) {
 #pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        col(0, j, 0)[lane + 32 * e] = xr[e];
-                        col(0, j, 1)[lane + 32 * e] = vr[e];
-                    }
+                    for (int e = 0; e < E; ++e) col(0, j)[lane + 32 * e] = xr[e];
                 }
                 __syncthreads();
             }
             if (C > 1) {
-                // circle-method move: top row t_0 fixed; t_i -> top i+1 (t_{C-1} -> bottom
-                // C-1); b_0 -> top 1; b_i -> bottom i-1.  Pull incoming blocks through
-                // registers: read remote, cluster barrier, write local.
-                cluster.sync();
+                // circle-method move of whole blocks: top row t_0 fixed; t_i -> top i+1
+                // (t_{C-1} -> bottom C-1); b_0 -> top 1; b_i -> bottom i-1.  Incoming
+                // blocks are pulled chunk by chunk through registers: read remote,
+                // cluster barrier, write local.
                 int src_rank[2] = {-1, -1}, src_slot[2] = {0, 0};
                 if (rank == 1) { src_rank[0] = 0; src_slot[0] = 1; }
                 else if (rank >= 2) { src_rank[0] = rank - 1; src_slot[0] = 0; }
                 if (rank == C - 1) { src_rank[1] = C - 1; src_slot[1] = 0; }
                 else { src_rank[1] = rank + 1; src_slot[1] = 1; }
-                const int per_slot = b * 2 * WP;
-                constexpr int MAXR = 2 * E;   // b <= JW, so a slot is <= 2E values per thread
-                T reg[2][MAXR];
                 int ids[2] = {0, 0};
-                for (int slot = 0; slot < 2; ++slot) {
-                    if (src_rank[slot] < 0) continue;
-                    T* rbuf = cluster.map_shared_rank(buf, src_rank[slot]);
-                    const T* src = rbuf + size_t(src_slot[slot]) * per_slot;
-#pragma unroll
-                    for (int r = 0; r < MAXR; ++r) {
-                        const int e = tid + r * (JW * 32);
-                        if (e < per_slot) reg[slot][r] = src[e];
-                    }
-                    int* rid = cluster.map_shared_rank(blk_id, src_rank[slot]);
-                    ids[slot] = rid[src_slot[slot]];
-                }
                 cluster.sync();
-                for (int slot = 0; slot < 2; ++slot) {
-                    if (src_rank[slot] < 0) continue;
-                    T* dst = buf + size_t(slot) * per_slot;
+                for (int base = 0; base < per_slot; base += chunk) {
+                    T reg[2][MOVE_REGS];
+                    for (int slot = 0; slot < 2; ++slot) {
+                        if (src_rank[slot] < 0) continue;
+                        const T* src = cluster.map_shared_rank(buf, src_rank[slot]) +
+                                       size_t(src_slot[slot]) * per_slot;
 #pragma unroll
-                    for (int r = 0; r < MAXR; ++r) {
-                        const int e = tid + r * (JW * 32);
-                        if (e < per_slot) dst[e] = reg[slot][r];
+                        for (int r = 0; r < MOVE_REGS; ++r) {
+                            const int e = base + tid + r * (JW * 32);
+                            if (e < per_slot) reg[slot][r] = src[e];
+                        }
+                        if (base == 0) ids[slot] = cluster.map_shared_rank(blk_id, src_rank[slot])[src_slot[slot]];
+                    }
+                    cluster.sync();
+                    for (int slot = 0; slot < 2; ++slot) {
+                        if (src_rank[slot] < 0) continue;
+                        T* dst = buf + size_t(slot) * per_slot;
+#pragma unroll
+                        for (int r = 0; r < MOVE_REGS; ++r) {
+                            const int e = base + tid + r * (JW * 32);
+                            if (e < per_slot) dst[e] = reg[slot][r];
+                        }
                     }
                 }
                 __syncthreads();
@@ -254,10 +231,7 @@ __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
         if (any) rotated_s = 1;
         __syncthreads();
         const int par = sweep & 1;
-        if (tid == 0) {
-            int* f0 = cluster.map_shared_rank(&flags[0][0], 0);
-            f0[par * 16 + rank] = rotated_s;
-        }
+        if (tid == 0) cluster.map_shared_rank(&flags[0][0], 0)[par * 16 + rank] = rotated_s;
         cluster.sync();
         int tot = 0;
         {
@@ -276,20 +250,16 @@ __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
         for (int j = 0; j < b; ++j) {
             const int gc = blk * b + j;
             if (gc >= w) continue;
-            const T* x = col(slot, j, 0);
-            const T* v = col(slot, j, 1);
-            for (int l = tid; l < w; l += blockDim.x) {
-                Xout[int64_t(gc) * ldw + l] = x[l];
-                Vout[int64_t(gc) * ldw + l] = v[l];
-            }
+            const T* x = col(slot, j);
+            for (int l = tid; l < w; l += blockDim.x) Xout[int64_t(gc) * ldw + l] = x[l];
         }
     }
     cluster.sync();   // keep shared memory alive until remote readers are done
 }
 
-// lambda_j = |x_j| (FP64 accumulation) and a descending order (ties: lower index first).
+// sv_j = |x_j| (FP64 accumulation) and a descending order (ties: lower index first).
 template <typename T>
-__global__ void eig_rank_kernel(const T* X, int64_t ldw, int w, T* lam, int* order) {
+__global__ void eig_rank_kernel(const T* X, int64_t ldw, int w, T* lam, int* order, T* nrm) {
     extern __shared__ double lsh[];
     const int tid = threadIdx.x;
     for (int j = tid; j < w; j += blockDim.x) {
@@ -298,7 +268,10 @@ __global__ void eig_rank_kernel(const T* X, int64_t ldw, int w, T* lam, int* ord
             const double v = double(X[int64_t(j) * ldw + l]);
             s += v * v;
         }
-        lsh[j] = sqrt(s);
+        // NaN sorts last, so the ranks below always form a permutation of 0..w-1
+        const double v = sqrt(s);
+        lsh[j] = isnan(v) ? -1.0 : v;
+        nrm[j] = T(v);
     }
     __syncthreads();
     for (int j = tid; j < w; j += blockDim.x) {
@@ -313,18 +286,22 @@ __global__ void eig_rank_kernel(const T* X, int64_t ldw, int w, T* lam, int* ord
     }
 }
 
-// Vt row r = V column order[r] (V stored column-major: row j of the array = column j).
+// Vt row r = x_{order[r]} / |x_{order[r]}| (rows of X are its columns).
 template <typename T>
-__global__ void eig_gather_kernel(const T* V, int64_t ldw, int w, const int* order, T* Vt,
-                                  int64_t ldv) {
+__global__ void eig_gather_kernel(const T* X, int64_t ldw, int w, const int* order, const T* nrm,
+                                  T* Vt, int64_t ldv) {
     const int r = blockIdx.x;
-    const int j = order[r];
-    for (int l = threadIdx.x; l < w; l += blockDim.x) Vt[int64_t(r) * ldv + l] = V[int64_t(j) * ldw + l];
+    int j = order[r];
+    if (j < 0 || j >= w) j = r;   // defensive: order is a permutation of 0..w-1
+    const T nj = nrm[j];
+    const T inv = (nj > T(0) && isfinite(nj)) ? T(1) / nj : T(0);
+    for (int l = threadIdx.x; l < w; l += blockDim.x)
+        Vt[int64_t(r) * ldv + l] = X[int64_t(j) * ldw + l] * inv;
 }
 
 template <typename T, int E>
-cudaError_t launch_cluster(cudaStream_t st, int C, size_t smem, const T* M, int64_t ldm, int w,
-                           int b, T* X, T* V, int64_t ldw, int max_sweeps, T tol, int* status,
+cudaError_t launch_cluster(cudaStream_t st, int C, size_t smem, const T* Xin, int64_t ldx, int w,
+                           int b, T* X, int64_t ldw, int max_sweeps, T tol, int* status,
                            int* sweeps) {
     auto kern = jacobi_cluster_kernel<T, E>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -345,15 +322,16 @@ cudaError_t launch_cluster(cudaStream_t st, int C, size_t smem, const T* M, int6
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, M, ldm, w, b, X, V, ldw, max_sweeps, tol, status, sweeps);
+    return cudaLaunchKernelEx(&cfg, kern, Xin, ldx, w, b, X, ldw, max_sweeps, tol, status, sweeps);
 }
 
 }  // namespace
 
-// Plan: cluster size C (power of two <= 16) and the register tile E (elements per lane
-// per column, WP = 32 E >= w).  Returns false when w is too large for this solver.
+// Plan: cluster size C (power of two <= 16), block width b = ceil(w / 2C) and register
+// tile E (elements per lane per column, WP = 32 E >= w).  Returns false when w is too
+// large for this solver (shared memory per CTA would exceed 200 KB).
 bool jacobi_plan(int w, int elem_bytes, int& C, int& b, int& E, size_t& smem) {
-    static const int Es[] = {1, 2, 4, 8, 12, 16, 24};
+    static const int Es[] = {1, 2, 4, 8, 12, 16, 24, 32};
     E = 0;
     for (int e : Es)
         if (32 * e >= w) { E = e; break; }
@@ -362,17 +340,20 @@ bool jacobi_plan(int w, int elem_bytes, int& C, int& b, int& E, size_t& smem) {
     while (C < 16 && w / (2 * C) >= 16) C *= 2;   // about 16 columns per block
     for (;; C *= 2) {
         b = (w + 2 * C - 1) / (2 * C);
-        smem = size_t(2) * b * 2 * 32 * E * elem_bytes;
-        // b <= JW: one column per warp in the cross rounds, and a slot fits in 2E
-        // registers per thread during the block moves
-        if (smem <= 200 * 1024 && b <= JW) return true;
+        smem = size_t(2) * b * 32 * E * elem_bytes;
+        if (smem <= 200 * 1024) return true;
         if (C >= 16) return false;
     }
 }
 
+// One-sided Jacobi on X (w x w, column j given as row j of Xin).  The solver passes
+// X = R^T with R^T R = M, so the converged columns are U Sigma with U the eigenvectors
+// of M and Sigma its square-root eigenvalues; for a PSD X = M the column norms are the
+// eigenvalues themselves.  On return lam[0..w) holds the column norms in descending
+// order, nrm[j] the norm of column j, and Vt row i the matching normalised column.
 template <typename T>
-void sym_eig(Exec& ex, int w, const T* M, int64_t ldm, T* X, T* V, int64_t ldw, T* lam, T* Vt,
-             int64_t ldv, int* order, int max_sweeps, double tol, int* sweeps_dev) {
+void sym_eig(Exec& ex, int w, const T* Xin, int64_t ldx, T* X, int64_t ldw, T* lam, T* nrm,
+             T* Vt, int64_t ldv, int* order, int max_sweeps, double tol, int* sweeps_dev) {
     int C, b, E;
     size_t smem;
     if (!jacobi_plan(w, int(sizeof(T)), C, b, E, smem)) {
@@ -382,15 +363,12 @@ void sym_eig(Exec& ex, int w, const T* M, int64_t ldm, T* X, T* V, int64_t ldw, 
     const T ttol = T(tol > 0 ? tol : 4.0 * sqrt(double(w)) * (sizeof(T) == 8 ? 1.1102230246251565e-16
                                                                             : 5.960464477539063e-08));
     cudaError_t err = cudaErrorInvalidValue;
+#define BKS_JAC(EE) \
+    case EE: err = launch_cluster<T, EE>(ex.stream, C, smem, Xin, ldx, w, b, X, ldw, max_sweeps, ttol, ex.status, sweeps_dev); break;
     switch (E) {
-        case 1: err = launch_cluster<T, 1>(ex.stream, C, smem, M, ldm, w, b, X, V, ldw, max_sweeps, ttol, ex.status, sweeps_dev); break;
-        case 2: err = launch_cluster<T, 2>(ex.stream, C, smem, M, ldm, w, b, X, V, ldw, max_sweeps, ttol, ex.status, sweeps_dev); break;
-        case 4: err = launch_cluster<T, 4>(ex.stream, C, smem, M, ldm, w, b, X, V, ldw, max_sweeps, ttol, ex.status, sweeps_dev); break;
-        case 8: err = launch_cluster<T, 8>(ex.stream, C, smem, M, ldm, w, b, X, V, ldw, max_sweeps, ttol, ex.status, sweeps_dev); break;
-        case 12: err = launch_cluster<T, 12>(ex.stream, C, smem, M, ldm, w, b, X, V, ldw, max_sweeps, ttol, ex.status, sweeps_dev); break;
-        case 16: err = launch_cluster<T, 16>(ex.stream, C, smem, M, ldm, w, b, X, V, ldw, max_sweeps, ttol, ex.status, sweeps_dev); break;
-        case 24: err = launch_cluster<T, 24>(ex.stream, C, smem, M, ldm, w, b, X, V, ldw, max_sweeps, ttol, ex.status, sweeps_dev); break;
+        BKS_JAC(1) BKS_JAC(2) BKS_JAC(4) BKS_JAC(8) BKS_JAC(12) BKS_JAC(16) BKS_JAC(24) BKS_JAC(32)
     }
+#undef BKS_JAC
     ex.launches++;
     if (err != cudaSuccess) {
         cudaGetLastError();
@@ -400,14 +378,14 @@ void sym_eig(Exec& ex, int w, const T* M, int64_t ldm, T* X, T* V, int64_t ldw, 
     const size_t lsmem = size_t(w) * sizeof(double);
     if (lsmem > 48 * 1024)
         cudaFuncSetAttribute(eig_rank_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lsmem));
-    eig_rank_kernel<T><<<1, 1024, lsmem, ex.stream>>>(X, ldw, w, lam, order);
-    eig_gather_kernel<T><<<w, 128, 0, ex.stream>>>(V, ldw, w, order, Vt, ldv);
+    eig_rank_kernel<T><<<1, 1024, lsmem, ex.stream>>>(X, ldw, w, lam, order, nrm);
+    eig_gather_kernel<T><<<w, 128, 0, ex.stream>>>(X, ldw, w, order, nrm, Vt, ldv);
     ex.launches += 2;
 }
 
-template void sym_eig<float>(Exec&, int, const float*, int64_t, float*, float*, int64_t, float*,
+template void sym_eig<float>(Exec&, int, const float*, int64_t, float*, int64_t, float*, float*,
                              float*, int64_t, int*, int, double, int*);
-template void sym_eig<double>(Exec&, int, const double*, int64_t, double*, double*, int64_t,
+template void sym_eig<double>(Exec&, int, const double*, int64_t, double*, int64_t, double*,
                               double*, double*, int64_t, int*, int, double, int*);
 
 }  // namespace bks

@@ -130,7 +130,8 @@ void product(Exec& ex, const bks_matrix* A, bool trans, int c, const T* X, int64
 struct Plan {
     int64_t n, d, ldn, ldd;
     int k, q, w;
-    size_t Qt, Bt, Pit, W, Wtmp, part, gram, rfac, ct, Mm, JX, JV, lam, Vt, order, Vk, stat;
+    size_t Qt, Bt, QBt, Pit, W, Wtmp, Wb, Wbtmp, part, gram, rfac, ct, Rm, JX, lam, nrm, Vt,
+        order, Vk, stat;
     int64_t part_cap;
     size_t total;
 };
@@ -146,8 +147,10 @@ int64_t max_partials(int64_t n, int64_t d, int k, int w, int sms) {
     upd(w, k, n);        // projection coefficients
     upd(k, n, w);        // projection update, Z = Q Ubar_k
     upd(k, k, n);        // Gram
-    upd(w, w, d);        // M
-    upd(k, d, w);        // B Ubar_k
+    upd(w, k, d);        // d-space projection coefficients (QR of B)
+    upd(k, d, w);        // d-space projection update, B Ubar_k
+    upd(k, k, d);        // d-space Gram
+    upd(w, w, d);        // R = Q_B^T B
     if (p < int64_t(k) * k) p = int64_t(k) * k;   // FP64 Gram output always uses partials
     return p;
 }
@@ -160,18 +163,21 @@ Plan make_plan(int64_t n, int64_t d, int k, int q_eff, int w, size_t tb, int sms
     Arena a;
     p.Qt = a.take(size_t(w) * p.ldn * tb);
     p.Bt = a.take(size_t(w) * p.ldd * tb);
+    p.QBt = a.take(size_t(w) * p.ldd * tb);
     p.Pit = a.take(size_t(k) * p.ldd * tb);
     p.W = a.take(size_t(k) * p.ldn * tb);
     p.Wtmp = a.take(size_t(k) * p.ldn * tb);
+    p.Wb = a.take(size_t(k) * p.ldd * tb);
+    p.Wbtmp = a.take(size_t(k) * p.ldd * tb);
     p.part_cap = max_partials(n, d, k, w, sms);
     p.part = a.take(size_t(p.part_cap) * sizeof(double));
     p.gram = a.take(size_t(w) * k * sizeof(double));
     p.rfac = a.take(size_t(k) * k * tb);
     p.ct = a.take(size_t(k) * w * tb);
-    p.Mm = a.take(size_t(w) * w * tb);
+    p.Rm = a.take(size_t(w) * w * tb);
     p.JX = a.take(size_t(w) * w * tb);
-    p.JV = a.take(size_t(w) * w * tb);
     p.lam = a.take(size_t(w) * tb);
+    p.nrm = a.take(size_t(w) * tb);
     p.Vt = a.take(size_t(w) * w * tb);
     p.order = a.take(size_t(w) * sizeof(int));
     p.Vk = a.take(size_t(k) * p.ldd * tb);
@@ -243,17 +249,20 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
     char* base = static_cast<char*>(ctx->ws);
     T* Qt = reinterpret_cast<T*>(base + p.Qt);
     T* Bt = reinterpret_cast<T*>(base + p.Bt);
+    T* QBt = reinterpret_cast<T*>(base + p.QBt);
     T* Pit = reinterpret_cast<T*>(base + p.Pit);
     T* W = reinterpret_cast<T*>(base + p.W);
     T* Wtmp = reinterpret_cast<T*>(base + p.Wtmp);
+    T* Wb = reinterpret_cast<T*>(base + p.Wb);
+    T* Wbtmp = reinterpret_cast<T*>(base + p.Wbtmp);
     double* part = reinterpret_cast<double*>(base + p.part);
     double* gram = reinterpret_cast<double*>(base + p.gram);
     T* rfac = reinterpret_cast<T*>(base + p.rfac);
     T* ct = reinterpret_cast<T*>(base + p.ct);
-    T* Mm = reinterpret_cast<T*>(base + p.Mm);
+    T* Rm = reinterpret_cast<T*>(base + p.Rm);
     T* JX = reinterpret_cast<T*>(base + p.JX);
-    T* JV = reinterpret_cast<T*>(base + p.JV);
     T* lam = reinterpret_cast<T*>(base + p.lam);
+    T* nrm = reinterpret_cast<T*>(base + p.nrm);
     T* Vt = reinterpret_cast<T*>(base + p.Vt);
     int* order = reinterpret_cast<int*>(base + p.order);
     T* Vk = reinterpret_cast<T*>(base + p.Vk);
@@ -287,6 +296,15 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
                       stat + 2);
         prof.end(1, b);
     };
+    // QR of the kept blocks B_i in d-space (R = Q_B^T B preconditions the eigen-solve)
+    auto orth_b = [&](int m, const T* Bblk) {
+        const int b = prof.begin();
+        cudaMemcpyAsync(Wb, Bblk, size_t(k) * p.ldd * sizeof(T), cudaMemcpyDeviceToDevice,
+                        ctx->stream);
+        orth_block<T>(ex, d, p.ldd, QBt, m, Wb, k, Wbtmp, QBt + size_t(m) * p.ldd, part,
+                      p.part_cap, gram, rfac, ct, stat + 2);
+        prof.end(1, b);
+    };
 
     // a1 + a4: W_0 = A Pi, Q_0 = orth(W_0)
     prod(false, Pit, p.ldd, W, p.ldn);
@@ -295,6 +313,7 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
         T* Qprev = krylov ? Qt + size_t(i - 1) * k * p.ldn : Qt;
         T* Bprev = krylov ? Bt + size_t(i - 1) * k * p.ldd : Bt;
         prod(true, Qprev, p.ldn, Bprev, p.ldd);          // a2: B_{i-1} = A^T Q_{i-1}
+        if (krylov && !o.basis_only) orth_b((i - 1) * k, Bprev);
         prod(false, Bprev, p.ldd, W, p.ldn);              // a3: W_i = A B_{i-1}
         if (krylov)
             orth(i * k, Qt + size_t(i) * k * p.ldn);     // a4: project + CholeskyQR2
@@ -315,15 +334,20 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
             transpose_in<T>(ex, Bt, sizeof(T) == 8 ? BKS_F64 : BKS_F32, k, d, p.ldd, V, k);
         }
     } else {
-        GemmDesc gm{};   // a5: M = B^T B (w x w)
+        // a5: M = B^T B is used through a triangular factor: with B = Q_B R (block QR of
+        // the kept blocks), M = R^T R, R = Q_B^T B.  One-sided Jacobi on R^T converges to
+        // U Sigma with U the eigenvectors of M, in fewer sweeps than on M itself and
+        // without accumulating V (Drmac & Veselic's preconditioned Jacobi SVD).
+        orth_b(krylov ? q_eff * k : 0, Blast);
+        GemmDesc gm{};
         gm.M = w; gm.N = w; gm.K = d;
-        gm.X = Bt; gm.ldx = p.ldd; gm.Y = Bt; gm.ldy = p.ldd;
+        gm.X = QBt; gm.ldx = p.ldd; gm.Y = Bt; gm.ldy = p.ldd;
         gm.y_kmajor = true; gm.y_dtype = sizeof(T) == 8 ? BKS_F64 : BKS_F32;
-        gm.out = Mm; gm.ldo = w; gm.alpha = 1.0; gm.beta = 0.0;
+        gm.out = Rm; gm.ldo = w; gm.alpha = 1.0; gm.beta = 0.0;
         gemm_simt<T>(ex, gm, part, p.part_cap);
-        check_finite<T>(ex, Mm, int64_t(w) * w);
-        // a6: eigen-decomposition of M, descending
-        sym_eig<T>(ex, w, Mm, w, JX, JV, w, lam, Vt, w, order,
+        check_finite<T>(ex, Rm, int64_t(w) * w);
+        // a6: eigen-decomposition of M, descending (row j of Rm is column j of R^T)
+        sym_eig<T>(ex, w, Rm, w, JX, w, lam, nrm, Vt, w, order,
                    o.jacobi_max_sweeps > 0 ? o.jacobi_max_sweeps : 40, o.jacobi_tol, stat + 1);
         // a7: Z = Q Ubar_k (row-major n x k)
         GemmDesc gz{};
@@ -645,7 +669,7 @@ bks_status bks_sym_eig(bks_ctx* ctx, int dtype, int w, const void* M, int64_t ld
         return fail(ctx, BKS_ERR_UNSUPPORTED, "w exceeds the Jacobi solver's limit");
     DeviceGuard g(ctx->device);
     Arena a;
-    const size_t o_x = a.take(size_t(w) * w * tb), o_v = a.take(size_t(w) * w * tb),
+    const size_t o_x = a.take(size_t(w) * w * tb), o_nrm = a.take(size_t(w) * tb),
                  o_vt = a.take(size_t(w) * w * tb), o_ord = a.take(size_t(w) * 4),
                  o_stat = a.take(16);
     bks_status s = ensure_ws(ctx, a.off);
@@ -659,13 +683,13 @@ bks_status bks_sym_eig(bks_ctx* ctx, int dtype, int w, const void* M, int64_t ld
     cudaMemsetAsync(stat, 0, 16, ctx->stream);
     if (dtype == BKS_F64) {
         sym_eig<double>(ex, w, static_cast<const double*>(M), ldm, reinterpret_cast<double*>(base + o_x),
-                        reinterpret_cast<double*>(base + o_v), w, static_cast<double*>(lam),
+                        w, static_cast<double*>(lam), reinterpret_cast<double*>(base + o_nrm),
                         reinterpret_cast<double*>(base + o_vt), w, reinterpret_cast<int*>(base + o_ord),
                         40, 0.0, stat + 1);
         transpose_in<double>(ex, base + o_vt, BKS_F64, w, w, w, static_cast<double*>(U), ldu);
     } else {
         sym_eig<float>(ex, w, static_cast<const float*>(M), ldm, reinterpret_cast<float*>(base + o_x),
-                       reinterpret_cast<float*>(base + o_v), w, static_cast<float*>(lam),
+                       w, static_cast<float*>(lam), reinterpret_cast<float*>(base + o_nrm),
                        reinterpret_cast<float*>(base + o_vt), w, reinterpret_cast<int*>(base + o_ord),
                        40, 0.0, stat + 1);
         transpose_in<float>(ex, base + o_vt, BKS_F32, w, w, w, static_cast<float*>(U), ldu);

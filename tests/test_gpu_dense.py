@@ -107,15 +107,21 @@ def test_sym_eig(dtype, w):
 # ------------------------------------------------------------------ start block (a0)
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
 def test_device_generator_matches_oracle(dtype):
+    """The device generator (CUDA log/sincos in FP64) against the oracle's (glibc):
+    FP32 output agrees bit for bit except where the two libms' last-bit differences
+    straddle an FP32 rounding boundary; FP64 output agrees to a few ulp."""
     tdt = torch.float32 if dtype == np.float32 else torch.float64
     got = host(bk.gen_pi(77, 8000, 50, dtype=tdt, device="cuda")).astype(np.float64)
     ref = np.empty(8000 * 50)
     for p in range(8000 * 25):
         ref[2 * p], ref[2 * p + 1] = orng.gaussian_pair(77, p)
-    ref = ref.reshape(8000, 50).astype(dtype).astype(np.float64)
-    same = np.mean(got == ref)
-    assert same > 0.9999
-    assert np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1e-30)) <= 2 * EPS[dtype]
+    ref = ref.reshape(8000, 50)
+    if dtype == np.float32:
+        ref = ref.astype(np.float32).astype(np.float64)
+        assert np.mean(got == ref) > 0.9999
+        assert np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1e-30)) <= 2 * EPS[dtype]
+    else:
+        assert np.max(np.abs(got - ref)) <= 1e-14
 
 
 # --------------------------------------------------------------- end-to-end (a0-a9)
