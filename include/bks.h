@@ -82,7 +82,10 @@ typedef struct {
     int32_t jacobi_max_sweeps;  /* default 40 */
     double jacobi_tol;          /* rotation threshold |x_p.x_q| <= tol |x_p||x_q|; 0 = default */
     int32_t profile;            /* 1: record per-kernel-class CUDA-event times into bks_stats */
-    int32_t reserved[7];
+    int32_t product_path;       /* products with a dense A: 0 auto (tensor cores when the
+                                   operands meet the TMA alignment rules, else CUDA cores),
+                                   1 CUDA cores (SIMT) only */
+    int32_t reserved[6];
 } bks_opts;
 
 typedef struct {
@@ -166,11 +169,15 @@ bks_status bks_gen_pi_host(uint64_t seed, int64_t d, int k, float* out_host);
 /* One product with A (Sec. 4: the only access to A): trans = 0 gives Y = A X
  * (X d x c, Y n x c), trans = 1 gives Y = A^T X (X n x c, Y d x c).  X and Y are
  * stored COLUMN-major with leading dimension ldx / ldy (column j of X starts at
- * X + j*ldx), FP32 (FP64 for an FP64 matrix).  For a BF16 matrix, X is rounded to
- * BF16 unless `exact` is 1, in which case X is split into three BF16 parts and the
- * product is FP32-accurate.  Honours A->col_mean. */
+ * X + j*ldx), FP32 (FP64 for an FP64 matrix).  flags: BKS_MATMUL_EXACT (BF16 A only)
+ * splits X into three BF16 parts so the product is FP32-accurate instead of rounding X
+ * to BF16; BKS_MATMUL_SIMT forces the CUDA-core kernel instead of the tensor cores.
+ * Honours A->col_mean.  Synchronises the stream once at the end to read the device
+ * status word (BKS_ERR_TIMEOUT if a bounded pipeline wait gave up). */
+#define BKS_MATMUL_EXACT 1
+#define BKS_MATMUL_SIMT 2
 bks_status bks_matmul(bks_ctx* ctx, const bks_matrix* A, int trans, int c,
-                      const void* X, int64_t ldx, void* Y, int64_t ldy, int exact);
+                      const void* X, int64_t ldx, void* Y, int64_t ldy, int flags);
 
 /* Block orthonormalisation (Sec. 4.1/4.2 reorthonormalisation): W (len x c,
  * column-major, ldw) is projected twice against the m orthonormal columns of Qb

@@ -97,7 +97,7 @@ def dense_matrix(a) -> BksMatrix:
 
 
 def _opts(precision="auto", basis_only=False, sign_fix=True, profile=False, jacobi_tol=0.0,
-          jacobi_max_sweeps=40, refine=True):
+          jacobi_max_sweeps=40, refine=True, simt=False):
     o = BksOpts()
     B.load().bks_opts_default(ctypes.byref(o))
     o.precision = {"auto": B.PREC_AUTO, "f64": B.PREC_F64, "f32": B.PREC_F32,
@@ -108,6 +108,7 @@ def _opts(precision="auto", basis_only=False, sign_fix=True, profile=False, jaco
     o.jacobi_tol = float(jacobi_tol)
     o.jacobi_max_sweeps = int(jacobi_max_sweeps)
     o.refine = int(refine)
+    o.product_path = 1 if simt else 0
     return o
 
 
@@ -164,9 +165,10 @@ def _colmajor(x):
     return out
 
 
-def matmul(a, x, trans=False):
+def matmul(a, x, trans=False, simt=False, exact=False):
     """Y = A X (trans False) or Y = A^T X (trans True) through bks_matmul.  x is a
-    (rows x c) CUDA tensor; the result is (rows' x c) in x's dtype."""
+    (rows x c) CUDA tensor; the result is (rows' x c) in x's dtype.  simt forces the
+    CUDA-core kernel; exact asks for the FP32-accurate split product on a BF16 A."""
     torch = _torch()
     mat = dense_matrix(a)
     ctx = context(a.device)
@@ -175,7 +177,8 @@ def matmul(a, x, trans=False):
     yt = torch.empty((x.shape[1], rows_y), dtype=x.dtype, device=x.device)
     B.check(ctx.lib.bks_matmul(ctx.ptr, ctypes.byref(mat), int(trans), x.shape[1],
                                ctypes.c_void_p(xt.data_ptr()), xt.stride(0),
-                               ctypes.c_void_p(yt.data_ptr()), yt.stride(0), 0),
+                               ctypes.c_void_p(yt.data_ptr()), yt.stride(0),
+                               (1 if exact else 0) | (2 if simt else 0)),
             ctx.ptr, "bks_matmul")
     return yt.t()
 

@@ -67,6 +67,15 @@ template <typename T>
 void gemm_simt(Exec& ex, const GemmDesc& g, double* partials, int64_t partial_cap);
 int64_t gemm_partial_elems(int64_t M, int64_t N, int64_t K, int num_sms);
 
+// Tensor-core (tcgen05, 3xTF32) product with an FP32 dense A: Y = (A X)^T (trans false)
+// or (A^T X)^T (trans true), thin blocks column-major.  xh/xl: c x ldx scratch each;
+// part: tc_partial_floats(...) floats.  Returns false, launching nothing, when the
+// operands do not meet the TMA alignment rules.
+bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda, bool trans, int c,
+                    const float* X, int64_t ldx, float* Y, int64_t ldy, float* xh, float* xl,
+                    float* part, int64_t part_cap);
+int64_t tc_partial_floats(int64_t n, int64_t d, int c, int num_sms);
+
 // ------------------------------------------------------------------ building blocks
 template <typename T>
 void gen_pi_device(Exec& ex, uint64_t seed, int64_t d, int k, T* out, int64_t ld_row,

@@ -107,10 +107,29 @@ bks_status check_matrix(bks_ctx* ctx, const bks_matrix* A) {
     return fail(ctx, BKS_ERR_INVALID_ARG, "unknown matrix kind");
 }
 
-// Products with A, in precision T.
+// Scratch of the tensor-core product: hi/lo split of X and partial tiles.
+struct ProductWs {
+    float* xh = nullptr;
+    float* xl = nullptr;
+    float* tpart = nullptr;
+    int64_t tpart_cap = 0;
+    bool simt_only = false;
+};
+
+// Products with A, in precision T: the tcgen05 kernel for an FP32 dense A when the
+// operands meet its alignment rules, else the SIMT tile kernel.
 template <typename T>
 void product(Exec& ex, const bks_matrix* A, bool trans, int c, const T* X, int64_t ldx, T* Y,
-             int64_t ldy, double* part, int64_t cap) {
+             int64_t ldy, double* part, int64_t cap, const ProductWs& pw) {
+    if (sizeof(T) == 4 && A->dtype == BKS_F32 && !pw.simt_only && pw.xh != nullptr) {
+        const int before = ex.launches;
+        if (tc_product_f32(ex, static_cast<const float*>(A->vals), A->n, A->d, A->ld, trans, c,
+                           reinterpret_cast<const float*>(X), ldx, reinterpret_cast<float*>(Y), ldy,
+                           pw.xh, pw.xl, pw.tpart, pw.tpart_cap)) {
+            ex.product_launches += ex.launches - before;
+            return;
+        }
+    }
     GemmDesc g{};
     g.M = c;
     g.N = trans ? A->d : A->n;
@@ -130,6 +149,8 @@ void product(Exec& ex, const bks_matrix* A, bool trans, int c, const T* X, int64
 struct Plan {
     int64_t n, d, ldn, ldd;
     int k, q, w;
+    size_t xh, xl, tpart;
+    int64_t tpart_cap;
     size_t Qt, Bt, QBt, Pit, W, Wtmp, Wb, Wbtmp, part, gram, rfac, ct, Rm, JX, lam, nrm, Vt,
         order, Vk, stat;
     int64_t part_cap;
@@ -181,6 +202,11 @@ Plan make_plan(int64_t n, int64_t d, int k, int q_eff, int w, size_t tb, int sms
     p.Vt = a.take(size_t(w) * w * tb);
     p.order = a.take(size_t(w) * sizeof(int));
     p.Vk = a.take(size_t(k) * p.ldd * tb);
+    const int64_t ldmax = p.ldn > p.ldd ? p.ldn : p.ldd;
+    p.xh = a.take(size_t(k) * ldmax * 4);
+    p.xl = a.take(size_t(k) * ldmax * 4);
+    p.tpart_cap = tc_partial_floats(n, d, k, sms);
+    p.tpart = a.take(size_t(p.tpart_cap) * 4);
     p.stat = a.take(4 * sizeof(int));
     p.total = a.off;
     return p;
@@ -266,6 +292,12 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
     T* Vt = reinterpret_cast<T*>(base + p.Vt);
     int* order = reinterpret_cast<int*>(base + p.order);
     T* Vk = reinterpret_cast<T*>(base + p.Vk);
+    ProductWs pw;
+    pw.xh = reinterpret_cast<float*>(base + p.xh);
+    pw.xl = reinterpret_cast<float*>(base + p.xl);
+    pw.tpart = reinterpret_cast<float*>(base + p.tpart);
+    pw.tpart_cap = p.tpart_cap;
+    pw.simt_only = o.product_path == 1;
     int* stat = reinterpret_cast<int*>(base + p.stat);   // [status, sweeps, shifted]
     T* Z = static_cast<T*>(Zv);
     T* sigma = static_cast<T*>(sigv);
@@ -287,7 +319,7 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
 
     auto prod = [&](bool trans, const T* X, int64_t ldx, T* Y, int64_t ldy) {
         const int b = prof.begin();
-        product<T>(ex, A, trans, k, X, ldx, Y, ldy, part, p.part_cap);
+        product<T>(ex, A, trans, k, X, ldx, Y, ldy, part, p.part_cap, pw);
         prof.end(0, b);
     };
     auto orth = [&](int m, T* Qout) {
@@ -578,8 +610,7 @@ bks_status bks_gen_pi_host(uint64_t seed, int64_t d, int k, float* out_host) {
 }
 
 bks_status bks_matmul(bks_ctx* ctx, const bks_matrix* A, int trans, int c, const void* X,
-                      int64_t ldx, void* Y, int64_t ldy, int exact) {
-    (void)exact;
+                      int64_t ldx, void* Y, int64_t ldy, int flags) {
     if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
     bks_status s = check_matrix(ctx, A);
     if (s != BKS_OK) return s;
@@ -589,20 +620,41 @@ bks_status bks_matmul(bks_ctx* ctx, const bks_matrix* A, int trans, int c, const
     DeviceGuard g(ctx->device);
     const bool f64 = A->dtype == BKS_F64;
     const int64_t cap = gemm_partial_elems(c, rows_y, rows_x, ctx->num_sms);
-    s = ensure_ws(ctx, size_t(cap) * sizeof(double) + 256);
+    const int64_t tcap = tc_partial_floats(A->n, A->d, c < 128 ? c : 128, ctx->num_sms);
+    Arena ar;
+    const size_t o_part = ar.take(size_t(cap) * sizeof(double) + 8),
+                 o_xh = ar.take(size_t(c) * ldx * 4), o_xl = ar.take(size_t(c) * ldx * 4),
+                 o_tp = ar.take(size_t(tcap) * 4), o_stat = ar.take(16);
+    s = ensure_ws(ctx, ar.off);
     if (s != BKS_OK) return s;
     Exec ex;
     ex.stream = ctx->stream;
     ex.num_sms = ctx->num_sms;
-    double* part = static_cast<double*>(ctx->ws);
+    char* wsb = static_cast<char*>(ctx->ws);
+    double* part = reinterpret_cast<double*>(wsb + o_part);
+    ProductWs pw;
+    pw.xh = reinterpret_cast<float*>(wsb + o_xh);
+    pw.xl = reinterpret_cast<float*>(wsb + o_xl);
+    pw.tpart = reinterpret_cast<float*>(wsb + o_tp);
+    pw.tpart_cap = tcap;
+    pw.simt_only = (flags & BKS_MATMUL_SIMT) != 0;
+    int* stat = reinterpret_cast<int*>(wsb + o_stat);
+    ex.status = stat;
+    cudaMemsetAsync(stat, 0, 16, ctx->stream);
     if (f64)
         product<double>(ex, A, trans != 0, c, static_cast<const double*>(X), ldx,
-                        static_cast<double*>(Y), ldy, part, cap);
+                        static_cast<double*>(Y), ldy, part, cap, pw);
     else
         product<float>(ex, A, trans != 0, c, static_cast<const float*>(X), ldx,
-                       static_cast<float*>(Y), ldy, part, cap);
-    cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? BKS_OK : cuda_fail(ctx, e, "bks_matmul");
+                       static_cast<float*>(Y), ldy, part, cap, pw);
+    cudaError_t e = cudaMemcpyAsync(ctx->host_status, stat, sizeof(int), cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bks_matmul");
+    if (ctx->host_status[0] & ST_TIMEOUT)
+        return fail(ctx, BKS_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
+    return BKS_OK;
 }
 
 bks_status bks_orthonormalize(bks_ctx* ctx, int dtype, int64_t len, int m, int c, const void* Qb,

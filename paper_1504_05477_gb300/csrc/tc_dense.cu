@@ -1,0 +1,571 @@
+// Tensor-core products with a dense FP32 A (the hot path of Algorithms 1 and 2: every
+// iteration touches A only through A X and A^T X, Sec. 4):
+//   mode AX : Out (c x n, column-major thin block) = (A X)^T,   X a c x d thin block
+//   mode ATX: Out (c x d)                          = (A^T X)^T, X a c x n thin block
+// FP32 accuracy from TF32 tensor cores by a three-term split: with
+// hi(v) = v truncated to TF32 and lo(v) = v - hi(v) (exact in FP32),
+//   A X ~ hi(A) hi(X) + hi(A) lo(X) + lo(A) hi(X),
+// dropping only lo(A) lo(X) (relative 2^-22).  hi(X) and lo(X) are stacked as the two
+// halves of one N = 2cp operand, so hi(A) [hi(X) | lo(X)] is one MMA and
+// lo(A) hi(X) a second one accumulating into the first half.
+//
+// One persistent CTA per SM.  The (tile, 32-deep chunk) units of the whole product are
+// dealt out in equal contiguous ranges (stream-K); a tile cut between CTAs is summed
+// by a fix-up kernel in CTA order, so results are deterministic.
+//   warp 0      TMA: raw A tiles -> 6-deep ring
+//   warp 1      TMA: [hi(X) | lo(X)] tiles -> 2-deep operand ring
+//   warp 2      tcgen05.mma issue (one thread); owns the TMEM allocation
+//   warps 3-6   converters: raw A -> hi(A), lo(A) in the UMMA K-major 128B-swizzled
+//               layout (for A^T X this is also the transpose)
+//   warps 7-10  epilogue: tcgen05.ld the accumulator, add the halves, store
+// Every wait is bounded (1 s of globaltimer); on timeout the CTA records
+// ST_TIMEOUT, drains what it issued (bounded again), frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+
+namespace bks {
+namespace tc {
+
+constexpr int BM = 128;            // UMMA M: rows of D per tile
+constexpr int KC = 32;             // contraction depth per chunk (128 bytes of FP32)
+constexpr int RA = 6;              // raw A ring depth
+constexpr int OP = 2;              // operand ring depth
+constexpr int NWARP = 11;
+constexpr int NTHREADS = NWARP * 32;
+constexpr uint32_t TILE_BYTES = BM * KC * 4;   // 16 KB
+constexpr uint64_t WAIT_NS = 1000000000ull;    // 1 s
+
+struct Params {
+    int mode;          // 0: AX, 1: ATX
+    int c;             // real output columns (<= 128)
+    int cp;            // padded columns (32, 64, 96, 128)
+    int64_t rows_out;  // extent of the tiled dimension (n for AX, d for ATX)
+    int64_t tiles;     // ceil(rows_out / BM)
+    int64_t cpt;       // chunks per tile (contraction length / KC, rounded up)
+    float* out;        // c x ldo
+    int64_t ldo;
+    float* part;       // partial tiles: [grid][maxseg][cp][BM]
+    int maxseg;
+    int* status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(
+                     smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait: false on timeout (status flagged, abort raised) or when another role
+// already aborted.
+__device__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    while (true) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > WAIT_NS) {
+            atomicOr(status, ST_TIMEOUT);
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+        "{%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+// UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, 8-row atoms 1024 B apart.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    uint64_t d = uint64_t((saddr & 0x3FFFF) >> 4);
+    d |= uint64_t(16 >> 4) << 16;      // leading byte offset (unused for swizzled K-major)
+    d |= uint64_t(1024 >> 4) << 32;    // stride byte offset
+    d |= uint64_t(1) << 46;            // descriptor version
+    d |= uint64_t(2) << 61;            // 128-byte swizzle
+    return d;
+}
+// Instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major, M = 128.
+__host__ __device__ constexpr uint32_t idesc_tf32(int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ float tf32_hi(float v) {
+    return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+}
+
+struct Smem {
+    uint64_t raw_full[RA], raw_empty[RA];
+    uint64_t b_full[OP], op_empty[OP], conv_full[OP];
+    uint64_t acc_full[2], acc_empty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+// Units of CTA `cta`: [start, end) in the flattened (tile, chunk) order.
+__device__ __forceinline__ void unit_range(int64_t U, int G, int cta, int64_t& s, int64_t& e) {
+    s = (int64_t(cta) * U) / G;
+    e = (int64_t(cta + 1) * U) / G;
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    tc_product_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmXh,
+                      const __grid_constant__ CUtensorMap tmXl, Params p) {
+    extern __shared__ unsigned char smem_dyn[];
+    // 1024-byte alignment for the swizzled tiles
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+    const uint32_t b_bytes = uint32_t(2 * p.cp) * 128u;
+    unsigned char* raw = base;                                   // RA x 16 KB
+    unsigned char* hi = raw + RA * TILE_BYTES;                   // OP x 16 KB
+    unsigned char* lo = hi + OP * TILE_BYTES;                    // OP x 16 KB
+    unsigned char* bop = lo + OP * TILE_BYTES;                   // OP x b_bytes
+    Smem* sm = reinterpret_cast<Smem*>(bop + OP * b_bytes);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int G = gridDim.x, cta = blockIdx.x;
+    const int64_t U = p.tiles * p.cpt;
+    int64_t ustart, uend;
+    unit_range(U, G, cta, ustart, uend);
+    volatile int* abort_flag = &sm->abort_flag;
+
+    if (tid == 0) {
+        for (int i = 0; i < RA; ++i) { mbar_init(&sm->raw_full[i], 1); mbar_init(&sm->raw_empty[i], 4); }
+        for (int i = 0; i < OP; ++i) {
+            mbar_init(&sm->b_full[i], 1);
+            mbar_init(&sm->op_empty[i], 1);
+            mbar_init(&sm->conv_full[i], 4);
+        }
+        for (int i = 0; i < 2; ++i) { mbar_init(&sm->acc_full[i], 1); mbar_init(&sm->acc_empty[i], 4); }
+        mbar_init(&sm->drain, 1);
+        sm->abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_async_smem();
+    }
+    if (warp == 2) {   // TMEM: two accumulators of up to 256 columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&sm->tmem_base)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm->tmem_base;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------------- A producer
+        if (lane == 0) {
+            int last[RA];   // phase of the last load issued into each stage (-1: none)
+            for (int s = 0; s < RA; ++s) last[s] = -1;
+            int64_t i = 0;
+            for (int64_t u = ustart; u < uend; ++u, ++i) {
+                const int s = int(i % RA);
+                if (!wait_bar(&sm->raw_empty[s], uint32_t(((i / RA) & 1) ^ 1), abort_flag, p.status)) break;
+                const int64_t t = u / p.cpt, kc = u % p.cpt;
+                mbar_expect_tx(&sm->raw_full[s], TILE_BYTES);
+                if (p.mode == 0)   // AX: box {32 (d), 128 (n)}
+                    tma_load_2d(raw + s * TILE_BYTES, &tmA, int(kc * KC), int(t * BM), &sm->raw_full[s]);
+                else               // ATX: box {128 (d), 32 (n)}
+                    tma_load_2d(raw + s * TILE_BYTES, &tmA, int(t * BM), int(kc * KC), &sm->raw_full[s]);
+                last[s] = int((i / RA) & 1);
+            }
+            // every load issued has landed before shared memory is released (bounded)
+            for (int s = 0; s < RA; ++s) {
+                if (last[s] < 0) continue;
+                const uint64_t t0 = gtimer();
+                while (!mbar_try(&sm->raw_full[s], uint32_t(last[s])) && gtimer() - t0 < WAIT_NS) {
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------------- X producer
+        if (lane == 0) {
+            int last[OP];
+            for (int o = 0; o < OP; ++o) last[o] = -1;
+            int64_t i = 0;
+            for (int64_t u = ustart; u < uend; ++u, ++i) {
+                const int o = int(i % OP);
+                if (!wait_bar(&sm->op_empty[o], uint32_t(((i / OP) & 1) ^ 1), abort_flag, p.status)) break;
+                const int64_t kc = u % p.cpt;
+                mbar_expect_tx(&sm->b_full[o], b_bytes);
+                unsigned char* dst = bop + o * b_bytes;
+                tma_load_2d(dst, &tmXh, int(kc * KC), 0, &sm->b_full[o]);
+                tma_load_2d(dst + p.cp * 128, &tmXl, int(kc * KC), 0, &sm->b_full[o]);
+                last[o] = int((i / OP) & 1);
+            }
+            for (int o = 0; o < OP; ++o) {
+                if (last[o] < 0) continue;
+                const uint64_t t0 = gtimer();
+                while (!mbar_try(&sm->b_full[o], uint32_t(last[o])) && gtimer() - t0 < WAIT_NS) {
+                }
+            }
+        }
+    } else if (warp == 2) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t id_full = idesc_tf32(2 * p.cp), id_half = idesc_tf32(p.cp);
+            int64_t i = 0;
+            int seg = -1;
+            int64_t cur_tile = -1;
+            bool first = true;
+            for (int64_t u = ustart; u < uend; ++u, ++i) {
+                const int64_t t = u / p.cpt;
+                if (t != cur_tile) {
+                    cur_tile = t;
+                    ++seg;
+                    if (!wait_bar(&sm->acc_empty[seg & 1], uint32_t(((seg >> 1) & 1) ^ 1), abort_flag, p.status)) break;
+                    tc_fence_after();
+                    first = true;
+                }
+                const int o = int(i % OP);
+                const uint32_t par = uint32_t((i / OP) & 1);
+                if (!wait_bar(&sm->conv_full[o], par, abort_flag, p.status)) break;
+                if (!wait_bar(&sm->b_full[o], par, abort_flag, p.status)) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + uint32_t((seg & 1) * 256);
+                const uint64_t dh = desc_sw128(smem_u32(hi + o * TILE_BYTES));
+                const uint64_t dl = desc_sw128(smem_u32(lo + o * TILE_BYTES));
+                const uint64_t db = desc_sw128(smem_u32(bop + o * b_bytes));
+#pragma unroll
+                for (int kk = 0; kk < KC / 8; ++kk) {   // K = 8 per tf32 MMA = 32 bytes
+                    const uint64_t adv = uint64_t(kk * 2);
+                    mma_tf32(d_tmem, dh + adv, db + adv, id_full, (first && kk == 0) ? 0u : 1u);
+                    mma_tf32(d_tmem, dl + adv, db + adv, id_half, 1u);
+                }
+                first = false;
+                umma_commit(&sm->op_empty[o]);
+                const bool last_of_seg = (u + 1 == uend) || ((u + 1) / p.cpt != t);
+                if (last_of_seg) umma_commit(&sm->acc_full[seg & 1]);
+            }
+            // drain: every MMA issued so far has completed before TMEM is released
+            umma_commit(&sm->drain);
+            wait_bar(&sm->drain, 0, abort_flag, p.status);
+        }
+    } else if (warp <= 6) {
+        // ---------------------------------------------------------------- converters
+        const int ct = tid - 96;   // 0..127
+        int64_t i = 0;
+        for (int64_t u = ustart; u < uend; ++u, ++i) {
+            const int s = int(i % RA), o = int(i % OP);
+            if (!wait_bar(&sm->raw_full[s], uint32_t((i / RA) & 1), abort_flag, p.status)) break;
+            if (!wait_bar(&sm->op_empty[o], uint32_t(((i / OP) & 1) ^ 1), abort_flag, p.status)) break;
+            const unsigned char* rs = raw + s * TILE_BYTES;
+            unsigned char* hs = hi + o * TILE_BYTES;
+            unsigned char* ls = lo + o * TILE_BYTES;
+            if (p.mode == 0) {
+                // same 128B-swizzled K-major layout in and out: elementwise on 16-byte chunks
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int off = (ct + 128 * q) * 16;
+                    const float4 v = *reinterpret_cast<const float4*>(rs + off);
+                    float4 h, l;
+                    h.x = tf32_hi(v.x); h.y = tf32_hi(v.y); h.z = tf32_hi(v.z); h.w = tf32_hi(v.w);
+                    l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
+                    *reinterpret_cast<float4*>(hs + off) = h;
+                    *reinterpret_cast<float4*>(ls + off) = l;
+                }
+            } else {
+                // raw tile: 32 rows (contraction) x 128 columns (M), row pitch 512 B.
+                // Thread ct owns M-row ct; it gathers 4 contraction values per 16-byte chunk.
+                const float* rf = reinterpret_cast<const float*>(rs);
+                const int rowoff = (ct >> 3) * 1024 + (ct & 7) * 128;
+#pragma unroll
+                for (int g = 0; g < 8; ++g) {
+                    float4 v;
+                    v.x = rf[(4 * g + 0) * BM + ct];
+                    v.y = rf[(4 * g + 1) * BM + ct];
+                    v.z = rf[(4 * g + 2) * BM + ct];
+                    v.w = rf[(4 * g + 3) * BM + ct];
+                    float4 h, l;
+                    h.x = tf32_hi(v.x); h.y = tf32_hi(v.y); h.z = tf32_hi(v.z); h.w = tf32_hi(v.w);
+                    l.x = v.x - h.x; l.y = v.y - h.y; l.z = v.z - h.z; l.w = v.w - h.w;
+                    const int off = rowoff + ((g ^ (ct & 7)) << 4);
+                    *reinterpret_cast<float4*>(hs + off) = h;
+                    *reinterpret_cast<float4*>(ls + off) = l;
+                }
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&sm->raw_empty[s]);
+                mbar_arrive(&sm->conv_full[o]);
+            }
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const int grp = warp & 3;                 // TMEM lanes 32*grp .. 32*grp+31
+        const int m = grp * 32 + lane;            // row of D owned by this thread
+        int seg = -1;
+        int64_t u = ustart;
+        while (u < uend) {
+            const int64_t t = u / p.cpt;
+            const int64_t seg_end = (t + 1) * p.cpt < uend ? (t + 1) * p.cpt : uend;
+            const bool whole = (u == t * p.cpt) && (seg_end == (t + 1) * p.cpt);
+            ++seg;
+            if (!wait_bar(&sm->acc_full[seg & 1], uint32_t((seg >> 1) & 1), abort_flag, p.status)) break;
+            tc_fence_after();
+            const uint32_t acc = tmem + uint32_t((seg & 1) * 256) + (uint32_t(grp * 32) << 16);
+            const int64_t row = t * BM + m;
+            float* dst;
+            int64_t stride;
+            if (whole) {
+                dst = p.out + row;
+                stride = p.ldo;
+            } else {
+                const int64_t slot = int64_t(cta) * p.maxseg + seg;
+                dst = p.part + slot * int64_t(p.cp) * BM + m;
+                stride = BM;
+            }
+            for (int j0 = 0; j0 < p.cp; j0 += 32) {
+                float h[32], l[32];
+                tmem_ld32(acc + uint32_t(j0), h);
+                tmem_ld32(acc + uint32_t(p.cp + j0), l);
+                if (!whole || row < p.rows_out) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (j0 + j < p.c) dst[int64_t(j0 + j) * stride] = h[j] + l[j];
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm->acc_empty[seg & 1]);
+            u = seg_end;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 2) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    }
+}
+
+// Tiles cut between CTAs: out[j][t*BM + m] = sum over the covering CTAs, in CTA order.
+// The CTA owning unit u is floor(((u + 1) G - 1) / U) for the ranges of unit_range.
+__global__ void tc_fixup_kernel(Params p, int G) {
+    const int64_t t = blockIdx.x;
+    const int m = threadIdx.x;
+    const int64_t U = p.tiles * p.cpt;
+    const int64_t u0 = t * p.cpt, u1 = (t + 1) * p.cpt - 1;
+    const int64_t c_first = ((u0 + 1) * G - 1) / U, c_last = ((u1 + 1) * G - 1) / U;
+    if (c_first == c_last) return;   // one CTA wrote the whole tile
+    const int64_t row = t * BM + m;
+    if (row >= p.rows_out) return;
+    for (int j = 0; j < p.c; ++j) {
+        float s = 0.f;
+        for (int64_t cc = c_first; cc <= c_last; ++cc) {
+            const int64_t start = (cc * U) / G;
+            const int64_t seg = t - start / p.cpt;
+            s += p.part[((cc * p.maxseg + seg) * p.cp + j) * BM + m];
+        }
+        p.out[int64_t(j) * p.ldo + row] = s;
+    }
+}
+
+// hi/lo split of a thin block (rows x len, row pitch ld).
+__global__ void tf32_split_kernel(const float* __restrict__ x, int rows, int64_t len, int64_t ld,
+                                  float* __restrict__ xh, float* __restrict__ xl) {
+    const int64_t total = int64_t(rows) * len;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t r = e / len, l = e % len;
+        const float v = x[r * ld + l];
+        const float h = tf32_hi(v);
+        xh[r * ld + l] = h;
+        xl[r * ld + l] = v - h;
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+bool encode_2d(CUtensorMap* map, const void* ptr, uint64_t inner, uint64_t outer,
+               uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle sw) {
+    auto fn = encode_fn();
+    if (fn == nullptr) return false;
+    if ((reinterpret_cast<uintptr_t>(ptr) & 15) != 0 || (row_bytes & 15) != 0) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {row_bytes};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t smem_bytes(int cp) {
+    return size_t(RA) * TILE_BYTES + size_t(2 * OP) * TILE_BYTES + size_t(OP) * 2 * cp * 128 +
+           sizeof(Smem) + 1024;
+}
+
+}  // namespace tc
+
+// Product with an FP32 A on the tensor cores.  Returns false (nothing launched) when the
+// operands do not meet the TMA alignment rules; the caller then uses the SIMT kernel.
+bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda, bool trans, int c,
+                    const float* X, int64_t ldx, float* Y, int64_t ldy, float* xh, float* xl,
+                    float* part, int64_t part_cap) {
+    using namespace tc;
+    if (c < 1) return true;
+    if ((reinterpret_cast<uintptr_t>(A) & 15) || ((lda * 4) & 15) || (reinterpret_cast<uintptr_t>(X) & 15) ||
+        ((ldx * 4) & 15) || (reinterpret_cast<uintptr_t>(xh) & 15) || (reinterpret_cast<uintptr_t>(xl) & 15))
+        return false;
+    const int64_t len = trans ? n : d;          // contraction length
+    const int64_t rows_out = trans ? d : n;     // tiled output dimension
+    if (len > INT32_MAX || rows_out > INT32_MAX) return false;
+    CUtensorMap tmA;
+    if (!trans) {
+        if (!encode_2d(&tmA, A, uint64_t(d), uint64_t(n), uint64_t(lda) * 4, KC, BM, CU_TENSOR_MAP_SWIZZLE_128B))
+            return false;
+    } else {
+        if (!encode_2d(&tmA, A, uint64_t(d), uint64_t(n), uint64_t(lda) * 4, BM, KC, CU_TENSOR_MAP_SWIZZLE_NONE))
+            return false;
+    }
+    const int G = ex.num_sms;
+    for (int c0 = 0; c0 < c; c0 += 128) {
+        const int cg = c - c0 < 128 ? c - c0 : 128;
+        const int cp = (cg + 31) / 32 * 32;
+        const float* Xg = X + int64_t(c0) * ldx;
+        float* xhg = xh + int64_t(c0) * ldx;
+        float* xlg = xl + int64_t(c0) * ldx;
+        {
+            const int64_t total = int64_t(cg) * len;
+            int blocks = int((total + 255) / 256);
+            if (blocks > 4 * G) blocks = 4 * G;
+            tf32_split_kernel<<<blocks, 256, 0, ex.stream>>>(Xg, cg, len, ldx, xhg, xlg);
+            ex.launches++;
+        }
+        CUtensorMap tmXh, tmXl;
+        if (!encode_2d(&tmXh, xhg, uint64_t(len), uint64_t(cg), uint64_t(ldx) * 4, KC, uint32_t(cp),
+                       CU_TENSOR_MAP_SWIZZLE_128B) ||
+            !encode_2d(&tmXl, xlg, uint64_t(len), uint64_t(cg), uint64_t(ldx) * 4, KC, uint32_t(cp),
+                       CU_TENSOR_MAP_SWIZZLE_128B))
+            return false;
+        Params p{};
+        p.mode = trans ? 1 : 0;
+        p.c = cg;
+        p.cp = cp;
+        p.rows_out = rows_out;
+        p.tiles = (rows_out + BM - 1) / BM;
+        p.cpt = (len + KC - 1) / KC;
+        p.out = Y + int64_t(c0) * ldy;
+        p.ldo = ldy;
+        const int64_t U = p.tiles * p.cpt;
+        const int64_t per = (U + G - 1) / G;
+        p.maxseg = int(per / p.cpt + 2);
+        if (int64_t(G) * p.maxseg * cp * BM > part_cap) return false;
+        p.part = part;
+        p.status = ex.status;
+        const size_t smem = smem_bytes(cp);
+        if (cudaFuncSetAttribute(tc_product_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(smem)) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        tc_product_kernel<<<G, NTHREADS, smem, ex.stream>>>(tmA, tmXh, tmXl, p);
+        tc_fixup_kernel<<<unsigned(p.tiles), BM, 0, ex.stream>>>(p, G);
+        ex.launches += 2;
+    }
+    return true;
+}
+
+int64_t tc_partial_floats(int64_t n, int64_t d, int c, int num_sms) {
+    int64_t best = 0;
+    for (int trans = 0; trans < 2; ++trans) {
+        const int64_t len = trans ? n : d, rows_out = trans ? d : n;
+        const int cp = ((c < 128 ? c : 128) + 31) / 32 * 32;
+        const int64_t tiles = (rows_out + tc::BM - 1) / tc::BM, cpt = (len + tc::KC - 1) / tc::KC;
+        const int64_t U = tiles * cpt, per = (U + num_sms - 1) / num_sms;
+        const int64_t need = int64_t(num_sms) * (per / cpt + 2) * cp * tc::BM;
+        if (need > best) best = need;
+    }
+    return best;
+}
+
+}  // namespace bks

@@ -52,6 +52,27 @@ def test_products_match_fp64(dtype, n, d, c, trans):
     assert np.all(np.abs(y - ref) <= bound + 1e-300)
 
 
+@pytest.mark.parametrize("n,d,c", [(1000, 308, 7), (4093, 1028, 50), (257, 96, 33),
+                                   (3001, 2052, 64), (5000, 1000, 100), (1000, 500, 130)])
+@pytest.mark.parametrize("trans", [False, True])
+def test_tensor_core_products(n, d, c, trans):
+    """Shapes whose rows meet the TMA alignment rules take the tcgen05 3xTF32 path; ragged
+    tails in both the tiled and the contraction dimension, and more than 128 columns."""
+    rng = np.random.default_rng(n + 3 * d + c)
+    a = rng.standard_normal((n, d)).astype(np.float32)
+    x = rng.standard_normal((n if trans else d, c)).astype(np.float32)
+    ad, xd = dev(a), dev(x)
+    y = host(bk.matmul(ad, xd, trans=trans))
+    y2 = host(bk.matmul(ad, xd, trans=trans))
+    ys = host(bk.matmul(ad, xd, trans=trans, simt=True))
+    a64, x64 = a.astype(np.float64), x.astype(np.float64)
+    ref = (a64.T if trans else a64) @ x64
+    bound = (np.abs(a64.T if trans else a64) @ np.abs(x64)) * 4 * np.sqrt(x.shape[0]) * EPS[np.float32]
+    assert np.array_equal(y, y2)                       # deterministic
+    assert np.all(np.abs(y - ref) <= bound)
+    assert np.all(np.abs(ys - ref) <= bound)
+
+
 def test_products_full_size_20000x8000():
     a, _ = synth.dense_planted_noisy()
     rng = np.random.default_rng(5)
