@@ -95,7 +95,7 @@ void orth_block(Exec& ex, int64_t len, int64_t ld, const T* Qb, int m, T* W, int
                 int* shifted_flag);
 template <typename T>
 void cholqr_extra(Exec& ex, int64_t len, int64_t ld, T* Q, int c, double* partials, int64_t cap,
-                  double* gram, T* rfac, int* shifted_flag);
+                  double* gram, T* rfac, int* shifted_flag, T* tmp);
 // Jacobi launch plan (cluster size C, block width b, register tile E, shared bytes).
 bool jacobi_plan(int w, int elem_bytes, int& C, int& b, int& E, size_t& smem);
 

@@ -2,23 +2,26 @@
 // each block as it is computed; the span is unchanged in exact arithmetic).
 //   1. Block classical Gram-Schmidt, twice (BCGS2):  W <- W - Q (Q^T W)
 //   2. CholeskyQR, twice (CholeskyQR2):  G = W^T W,  G = R^T R,  W <- W R^{-1}
-// Gram matrices are accumulated in FP64 across CTAs; the Cholesky factorisation runs
-// in FP64 in one CTA; W R^{-1} is a row-parallel forward substitution.  A Gram
-// matrix whose Cholesky factorisation meets a non-positive pivot is retried with a
-// growing diagonal shift (shifted CholeskyQR, Fukaya et al. 2020) and a third
-// CholeskyQR pass then restores orthogonality.
+// Gram matrices are accumulated in FP64 across CTAs.  The c x c Cholesky factor and
+// its inverse are formed by one CTA in the path's precision (FP32 on the FP32 path:
+// the second CholeskyQR pass removes the orthogonality lost to the first pass's
+// rounding as long as cond(W) stays below about 1e3, which the two projections
+// ensure), and W R^{-1} runs as a parallel GEMM.  A factorisation that meets a
+// non-positive pivot is retried with a growing diagonal shift (shifted CholeskyQR,
+// Fukaya et al. 2020); the status word records the shift.
 #include "common.cuh"
 
 namespace bks {
 
 namespace {
 
-// G (c x c, FP64, row-major) -> R (c x c upper triangular, row-major, type T).
-// One CTA.  Right-looking factorisation on the upper triangle held in shared memory.
+// G (c x c, FP64, row-major, symmetric) -> P = R^{-T} (c x c row-major, type T), where
+// G = R^T R with R upper triangular; Q = W R^{-1} is then Q^T = P W^T.  One CTA.
 template <typename T>
-__global__ void chol_kernel(const double* __restrict__ G, int c, T* __restrict__ R,
-                            int* status, int* shifted_flag) {
-    extern __shared__ double S[];   // c*c
+__global__ void chol_inv_kernel(const double* __restrict__ G, int c, T* __restrict__ P,
+                                int* status, int* shifted_flag) {
+    extern __shared__ unsigned char smem_raw[];
+    T* S = reinterpret_cast<T*>(smem_raw);   // c*c: R (upper triangle)
     __shared__ int ok_s;
     __shared__ double trace_s;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -26,7 +29,7 @@ __global__ void chol_kernel(const double* __restrict__ G, int c, T* __restrict__
     for (int e = tid; e < c * c; e += nt) bad |= !isfinite(G[e]);
     if (__syncthreads_or(bad)) {
         if (tid == 0) atomicOr(status, ST_NONFINITE);
-        for (int e = tid; e < c * c; e += nt) R[e] = T((e / c == e % c) ? 1.0 : 0.0);
+        for (int e = tid; e < c * c; e += nt) P[e] = T((e / c == e % c) ? 1.0 : 0.0);
         return;
     }
     if (tid == 0) {
@@ -37,74 +40,57 @@ __global__ void chol_kernel(const double* __restrict__ G, int c, T* __restrict__
     __syncthreads();
     double shift = 0.0;
     for (int attempt = 0; attempt < 6; ++attempt) {
-        for (int e = tid; e < c * c; e += nt) {
-            const int a = e / c, b = e % c;
-            // use the upper triangle only (symmetric input)
-            S[e] = (a <= b) ? G[a * c + b] : 0.0;
-            if (a == b) S[e] += shift;
-        }
+        for (int a = 0; a < c; ++a)
+            for (int b = tid; b < c; b += nt)
+                S[a * c + b] = (a <= b) ? T(G[a * c + b] + (a == b ? shift : 0.0)) : T(0);
         if (tid == 0) ok_s = 1;
         __syncthreads();
         for (int j = 0; j < c; ++j) {
-            const double piv = S[j * c + j];
-            if (!(piv > 0.0) || !isfinite(piv)) {   // uniform: every thread sees the same value
+            const T piv = S[j * c + j];
+            if (!(piv > T(0)) || !isfinite(piv)) {   // uniform: every thread sees the same value
                 if (tid == 0) ok_s = 0;
                 break;
             }
-            const double rjj = sqrt(piv);
-            const double inv = 1.0 / rjj;
+            const T rjj = sqrt(piv);
+            const T inv = T(1) / rjj;
             __syncthreads();
             for (int l = j + 1 + tid; l < c; l += nt) S[j * c + l] *= inv;
             if (tid == 0) S[j * c + j] = rjj;
             __syncthreads();
-            const int m = c - j - 1;
             // trailing update of the upper triangle: S[a][b] -= R[j][a] R[j][b], j < a <= b
-            for (int e = tid; e < m * m; e += nt) {
-                const int a = j + 1 + e / m, b = j + 1 + e % m;
-                if (a <= b) S[a * c + b] -= S[j * c + a] * S[j * c + b];
+            // (16 x 16 thread grid over the trailing square)
+            const int ty = tid >> 4, tx = tid & 15;
+            for (int a = j + 1 + ty; a < c; a += 16) {
+                const T rja = S[j * c + a];
+                for (int b = j + 1 + tx; b < c; b += 16)
+                    if (a <= b) S[a * c + b] -= rja * S[j * c + b];
             }
             __syncthreads();
         }
         __syncthreads();
         if (ok_s) break;
-        // shifted CholeskyQR: grow the diagonal shift relative to the trace
-        shift = (shift == 0.0) ? 1e-12 * trace_s / c : shift * 1e3;
+        shift = (shift == 0.0) ? (sizeof(T) == 8 ? 1e-12 : 1e-6) * trace_s / c : shift * 1e3;
         if (tid == 0) atomicOr(shifted_flag, 1);
         __syncthreads();
     }
     if (!ok_s) {
         if (tid == 0) atomicOr(status, ST_BREAKDOWN);
-        for (int e = tid; e < c * c; e += nt) R[e] = T((e / c == e % c) ? 1.0 : 0.0);
+        for (int e = tid; e < c * c; e += nt) P[e] = T((e / c == e % c) ? 1.0 : 0.0);
         return;
     }
     if (shift > 0.0 && tid == 0) atomicOr(status, ST_SHIFTED);
-    for (int e = tid; e < c * c; e += nt) {
-        const int a = e / c, b = e % c;
-        R[e] = T(a <= b ? S[e] : 0.0);
+    // R^{-1} column by column: thread j solves R x = e_j by back substitution and keeps
+    // x in row j of P = R^{-T} (only thread j reads or writes that row)
+    for (int j = tid; j < c; j += nt) {
+        T* x = P + int64_t(j) * c;
+        for (int i = j + 1; i < c; ++i) x[i] = T(0);
+        x[j] = T(1) / S[j * c + j];
+        for (int i = j - 1; i >= 0; --i) {
+            T acc = T(0);
+            for (int l = i + 1; l <= j; ++l) acc = fma(S[i * c + l], x[l], acc);
+            x[i] = -acc / S[i * c + i];
+        }
     }
-}
-
-// Q = W R^{-1} row by row: for position r, q_j = (w_j - sum_{i<j} q_i R[i][j]) / R[j][j].
-// W and Q are column-major thin blocks (row j of the array = column j).  W == Q allowed.
-template <typename T>
-__global__ void trsm_rows_kernel(const T* W, int64_t ldw, const T* __restrict__ R, int c, T* Q,
-                                 int64_t ldq, int64_t len) {
-    extern __shared__ unsigned char smem_raw[];
-    T* Rs = reinterpret_cast<T*>(smem_raw);          // c*c
-    T* Ws = Rs + c * c;                              // c * blockDim.x
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int e = tid; e < c * c; e += nt) Rs[e] = R[e];
-    const int64_t r = int64_t(blockIdx.x) * nt + tid;
-    const bool live = r < len;
-    for (int j = 0; j < c; ++j) Ws[j * nt + tid] = live ? W[j * ldw + r] : T(0);
-    __syncthreads();
-    for (int j = 0; j < c; ++j) {
-        T acc = Ws[j * nt + tid];
-        for (int i = 0; i < j; ++i) acc = fma(-Ws[i * nt + tid], Rs[i * c + j], acc);
-        Ws[j * nt + tid] = acc / Rs[j * c + j];
-    }
-    if (live)
-        for (int j = 0; j < c; ++j) Q[j * ldq + r] = Ws[j * nt + tid];
 }
 
 template <typename T>
@@ -117,29 +103,25 @@ void cholqr_pass(Exec& ex, int64_t len, int64_t ld, const T* src, int c, T* dst,
     g.out = gram; g.ldo = c; g.out_transposed = false; g.out_f64 = true;
     g.alpha = 1.0; g.beta = 0.0;
     gemm_simt<T>(ex, g, partials, cap);
-    const size_t smem = size_t(c) * c * sizeof(double);
+    const size_t smem = size_t(c) * c * sizeof(T);
     if (smem > 48 * 1024)
-        cudaFuncSetAttribute(chol_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    chol_kernel<T><<<1, 256, smem, ex.stream>>>(gram, c, rfac, ex.status, shifted_flag);
+        cudaFuncSetAttribute(chol_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    chol_inv_kernel<T><<<1, 256, smem, ex.stream>>>(gram, c, rfac, ex.status, shifted_flag);
     ex.launches++;
-    int nt = 128;
-    size_t smem2 = size_t(c) * c * sizeof(T) + size_t(c) * nt * sizeof(T);
-    while (smem2 > 200 * 1024 && nt > 32) {
-        nt /= 2;
-        smem2 = size_t(c) * c * sizeof(T) + size_t(c) * nt * sizeof(T);
-    }
-    if (smem2 > 48 * 1024)
-        cudaFuncSetAttribute(trsm_rows_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(smem2));
-    trsm_rows_kernel<T><<<unsigned((len + nt - 1) / nt), nt, smem2, ex.stream>>>(src, ld, rfac, c,
-                                                                                  dst, ld, len);
-    ex.launches++;
+    GemmDesc ga{};   // dst^T = P src^T: row a of dst = sum_b P[a][b] row b of src
+    ga.M = c; ga.N = len; ga.K = c;
+    ga.X = rfac; ga.ldx = c; ga.Y = src; ga.ldy = ld;
+    ga.y_kmajor = false; ga.y_dtype = sizeof(T) == 8 ? 0 : 1;
+    ga.out = dst; ga.ldo = ld; ga.out_transposed = false;
+    ga.alpha = 1.0; ga.beta = 0.0;
+    gemm_simt<T>(ex, ga, partials, cap);
 }
 
 }  // namespace
 
-// W (c x ld) against Qb (m x ld): BCGS2 then CholeskyQR2, result in Qout.  Wtmp holds
-// the first CholeskyQR iterate; `ct` (c x m, type T) the projection coefficients.
+// W (c x ld) against Qb (m x ld): BCGS2 then CholeskyQR2, result in Qout (Qout != W).
+// Wtmp holds the first CholeskyQR iterate; `ct` (c x m, type T) the projection
+// coefficients; `rfac` (c x c) the inverse Cholesky factor.
 template <typename T>
 void orth_block(Exec& ex, int64_t len, int64_t ld, const T* Qb, int m, T* W, int c, T* Wtmp,
                 T* Qout, double* partials, int64_t cap, double* gram, T* rfac, T* ct,
@@ -167,18 +149,18 @@ void orth_block(Exec& ex, int64_t len, int64_t ld, const T* Qb, int m, T* W, int
     cholqr_pass<T>(ex, len, ld, Wtmp, c, Qout, partials, cap, gram, rfac, shifted_flag);
 }
 
-// A third CholeskyQR pass in place (after a shifted factorisation).
 template <typename T>
 void cholqr_extra(Exec& ex, int64_t len, int64_t ld, T* Q, int c, double* partials, int64_t cap,
-                  double* gram, T* rfac, int* shifted_flag) {
-    cholqr_pass<T>(ex, len, ld, Q, c, Q, partials, cap, gram, rfac, shifted_flag);
+                  double* gram, T* rfac, int* shifted_flag, T* tmp) {
+    cholqr_pass<T>(ex, len, ld, Q, c, tmp, partials, cap, gram, rfac, shifted_flag);
+    cudaMemcpyAsync(Q, tmp, size_t(c) * ld * sizeof(T), cudaMemcpyDeviceToDevice, ex.stream);
 }
 
 #define BKS_INST(T)                                                                          \
     template void orth_block<T>(Exec&, int64_t, int64_t, const T*, int, T*, int, T*, T*,     \
                                 double*, int64_t, double*, T*, T*, int*);                    \
     template void cholqr_extra<T>(Exec&, int64_t, int64_t, T*, int, double*, int64_t,        \
-                                  double*, T*, int*);
+                                  double*, T*, int*, T*);
 BKS_INST(float)
 BKS_INST(double)
 #undef BKS_INST

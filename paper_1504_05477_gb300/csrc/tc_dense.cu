@@ -427,6 +427,7 @@ __global__ void tc_fixup_kernel(Params p, int G) {
         float s = 0.f;
         for (int64_t cc = c_first; cc <= c_last; ++cc) {
             const int64_t start = (cc * U) / G;
+            if (((cc + 1) * U) / G == start) continue;   // a CTA with no units wrote nothing
             const int64_t seg = t - start / p.cpt;
             s += p.part[((cc * p.maxseg + seg) * p.cp + j) * BM + m];
         }
@@ -537,9 +538,10 @@ bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda,
         p.out = Y + int64_t(c0) * ldy;
         p.ldo = ldy;
         const int64_t U = p.tiles * p.cpt;
-        const int64_t per = (U + G - 1) / G;
+        const int Gc = U < G ? int(U) : G;   // every CTA gets at least one unit
+        const int64_t per = (U + Gc - 1) / Gc;
         p.maxseg = int(per / p.cpt + 2);
-        if (int64_t(G) * p.maxseg * cp * BM > part_cap) return false;
+        if (int64_t(Gc) * p.maxseg * cp * BM > part_cap) return false;
         p.part = part;
         p.status = ex.status;
         const size_t smem = smem_bytes(cp);
@@ -548,8 +550,8 @@ bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda,
             cudaGetLastError();
             return false;
         }
-        tc_product_kernel<<<G, NTHREADS, smem, ex.stream>>>(tmA, tmXh, tmXl, p);
-        tc_fixup_kernel<<<unsigned(p.tiles), BM, 0, ex.stream>>>(p, G);
+        tc_product_kernel<<<Gc, NTHREADS, smem, ex.stream>>>(tmA, tmXh, tmXl, p);
+        tc_fixup_kernel<<<unsigned(p.tiles), BM, 0, ex.stream>>>(p, Gc);
         ex.launches += 2;
     }
     return true;
