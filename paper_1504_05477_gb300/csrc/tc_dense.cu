@@ -36,6 +36,7 @@ constexpr int NWARP = 11;
 constexpr int NTHREADS = NWARP * 32;
 constexpr uint32_t TILE_BYTES = BM * KC * 4;   // 16 KB
 constexpr uint64_t WAIT_NS = 1000000000ull;    // 1 s
+constexpr int FLUSH = 4;           // chunks (32 tf32 MMA steps) per TMEM accumulation window
 
 struct Params {
     int mode;          // 0: AX, 1: ATX
@@ -178,6 +179,13 @@ __device__ __forceinline__ void unit_range(int64_t U, int G, int cta, int64_t& s
     e = (int64_t(cta + 1) * U) / G;
 }
 
+// A new accumulation window starts at the CTA's first unit, at every tile boundary and
+// every FLUSH chunks within a tile.
+__device__ __forceinline__ bool window_start(int64_t u, int64_t ustart, int64_t cpt) {
+    return u == ustart || (u % cpt) % FLUSH == 0;
+}
+
+template <int CP>
 __global__ void __launch_bounds__(NTHREADS, 1)
     tc_product_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmXh,
                       const __grid_constant__ CUtensorMap tmXl, Params p) {
@@ -185,7 +193,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // 1024-byte alignment for the swizzled tiles
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
-    const uint32_t b_bytes = uint32_t(2 * p.cp) * 128u;
+    const uint32_t b_bytes = uint32_t(2 * CP) * 128u;
     unsigned char* raw = base;                                   // RA x 16 KB
     unsigned char* hi = raw + RA * TILE_BYTES;                   // OP x 16 KB
     unsigned char* lo = hi + OP * TILE_BYTES;                    // OP x 16 KB
@@ -261,7 +269,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 mbar_expect_tx(&sm->b_full[o], b_bytes);
                 unsigned char* dst = bop + o * b_bytes;
                 tma_load_2d(dst, &tmXh, int(kc * KC), 0, &sm->b_full[o]);
-                tma_load_2d(dst + p.cp * 128, &tmXl, int(kc * KC), 0, &sm->b_full[o]);
+                tma_load_2d(dst + CP * 128, &tmXl, int(kc * KC), 0, &sm->b_full[o]);
                 last[o] = int((i / OP) & 1);
             }
             for (int o = 0; o < OP; ++o) {
@@ -274,26 +282,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else if (warp == 2) {
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
-            const uint32_t id_full = idesc_tf32(2 * p.cp), id_half = idesc_tf32(p.cp);
+            const uint32_t id_full = idesc_tf32(2 * CP), id_half = idesc_tf32(CP);
             int64_t i = 0;
-            int seg = -1;
-            int64_t cur_tile = -1;
+            int sub = -1;   // accumulation window: at most FLUSH chunks per TMEM accumulator
             bool first = true;
             for (int64_t u = ustart; u < uend; ++u, ++i) {
                 const int64_t t = u / p.cpt;
-                if (t != cur_tile) {
-                    cur_tile = t;
-                    ++seg;
-                    if (!wait_bar(&sm->acc_empty[seg & 1], uint32_t(((seg >> 1) & 1) ^ 1), abort_flag, p.status)) break;
+                if (window_start(u, ustart, p.cpt)) {
+                    ++sub;
+                    if (!wait_bar(&sm->acc_empty[sub & 1], uint32_t(((sub >> 1) & 1) ^ 1), abort_flag, p.status)) break;
                     tc_fence_after();
                     first = true;
                 }
+                (void)t;
                 const int o = int(i % OP);
                 const uint32_t par = uint32_t((i / OP) & 1);
                 if (!wait_bar(&sm->conv_full[o], par, abort_flag, p.status)) break;
                 if (!wait_bar(&sm->b_full[o], par, abort_flag, p.status)) break;
                 tc_fence_after();
-                const uint32_t d_tmem = tmem + uint32_t((seg & 1) * 256);
+                const uint32_t d_tmem = tmem + uint32_t((sub & 1) * 256);
                 const uint64_t dh = desc_sw128(smem_u32(hi + o * TILE_BYTES));
                 const uint64_t dl = desc_sw128(smem_u32(lo + o * TILE_BYTES));
                 const uint64_t db = desc_sw128(smem_u32(bop + o * b_bytes));
@@ -305,8 +312,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 first = false;
                 umma_commit(&sm->op_empty[o]);
-                const bool last_of_seg = (u + 1 == uend) || ((u + 1) / p.cpt != t);
-                if (last_of_seg) umma_commit(&sm->acc_full[seg & 1]);
+                if (u + 1 == uend || window_start(u + 1, ustart, p.cpt))
+                    umma_commit(&sm->acc_full[sub & 1]);
             }
             // drain: every MMA issued so far has completed before TMEM is released
             umma_commit(&sm->drain);
@@ -366,16 +373,46 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ---------------------------------------------------------------- epilogue
         const int grp = warp & 3;                 // TMEM lanes 32*grp .. 32*grp+31
         const int m = grp * 32 + lane;            // row of D owned by this thread
-        int seg = -1;
+        int seg = -1, sub = -1;
         int64_t u = ustart;
-        while (u < uend) {
+        bool ok = true;
+        while (u < uend && ok) {
             const int64_t t = u / p.cpt;
             const int64_t seg_end = (t + 1) * p.cpt < uend ? (t + 1) * p.cpt : uend;
             const bool whole = (u == t * p.cpt) && (seg_end == (t + 1) * p.cpt);
             ++seg;
-            if (!wait_bar(&sm->acc_full[seg & 1], uint32_t((seg >> 1) & 1), abort_flag, p.status)) break;
-            tc_fence_after();
-            const uint32_t acc = tmem + uint32_t((seg & 1) * 256) + (uint32_t(grp * 32) << 16);
+            // running sum of the tile segment in registers (round to nearest): every
+            // TMEM accumulator holds at most FLUSH chunks, so its truncating FP32
+            // accumulation never runs long enough to bias the result
+            float run[CP];
+#pragma unroll
+            for (int j = 0; j < CP; ++j) run[j] = 0.f;
+            while (u < seg_end) {
+                int64_t w_end = u + 1;
+                while (w_end < seg_end && !window_start(w_end, ustart, p.cpt)) ++w_end;
+                ++sub;
+                if (!wait_bar(&sm->acc_full[sub & 1], uint32_t((sub >> 1) & 1), abort_flag, p.status)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t acc = tmem + uint32_t((sub & 1) * 256) + (uint32_t(grp * 32) << 16);
+#pragma unroll
+                for (int j0 = 0; j0 < CP; j0 += 32) {
+                    float h[32];
+                    tmem_ld32(acc + uint32_t(j0), h);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) run[j0 + j] += h[j];
+                    tmem_ld32(acc + uint32_t(CP + j0), h);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) run[j0 + j] += h[j];
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm->acc_empty[sub & 1]);
+                u = w_end;
+            }
+            if (!ok) break;
             const int64_t row = t * BM + m;
             float* dst;
             int64_t stride;
@@ -384,23 +421,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 stride = p.ldo;
             } else {
                 const int64_t slot = int64_t(cta) * p.maxseg + seg;
-                dst = p.part + slot * int64_t(p.cp) * BM + m;
+                dst = p.part + slot * int64_t(CP) * BM + m;
                 stride = BM;
             }
-            for (int j0 = 0; j0 < p.cp; j0 += 32) {
-                float h[32], l[32];
-                tmem_ld32(acc + uint32_t(j0), h);
-                tmem_ld32(acc + uint32_t(p.cp + j0), l);
-                if (!whole || row < p.rows_out) {
+            if (!whole || row < p.rows_out) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (j0 + j < p.c) dst[int64_t(j0 + j) * stride] = h[j] + l[j];
-                }
+                for (int j = 0; j < CP; ++j)
+                    if (j < p.c) dst[int64_t(j) * stride] = run[j];
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sm->acc_empty[seg & 1]);
-            u = seg_end;
         }
     }
 
@@ -545,12 +573,23 @@ bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda,
         p.part = part;
         p.status = ex.status;
         const size_t smem = smem_bytes(cp);
-        if (cudaFuncSetAttribute(tc_product_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(smem)) != cudaSuccess) {
+        cudaError_t err;
+        switch (cp) {
+#define BKS_TC(CPV)                                                                         \
+    case CPV:                                                                               \
+        err = cudaFuncSetAttribute(tc_product_kernel<CPV>,                                  \
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)); \
+        if (err == cudaSuccess)                                                             \
+            tc_product_kernel<CPV><<<Gc, NTHREADS, smem, ex.stream>>>(tmA, tmXh, tmXl, p);  \
+        break;
+            BKS_TC(32) BKS_TC(64) BKS_TC(96) BKS_TC(128)
+#undef BKS_TC
+            default: err = cudaErrorInvalidValue;
+        }
+        if (err != cudaSuccess) {
             cudaGetLastError();
             return false;
         }
-        tc_product_kernel<<<Gc, NTHREADS, smem, ex.stream>>>(tmA, tmXh, tmXl, p);
         tc_fixup_kernel<<<unsigned(p.tiles), BM, 0, ex.stream>>>(p, Gc);
         ex.launches += 2;
     }

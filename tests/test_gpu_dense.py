@@ -73,6 +73,23 @@ def test_tensor_core_products(n, d, c, trans):
     assert np.all(np.abs(ys - ref) <= bound)
 
 
+@pytest.mark.parametrize("trans", [False, True])
+def test_tensor_core_products_unbiased(trans):
+    """All-positive data makes every partial sum grow coherently, so an accumulator that
+    rounds toward zero shows up as a one-sided relative error of order (steps x 2^-24).
+    Round-to-nearest accumulation stays within ~sqrt(K) eps of the exact sum."""
+    rng = np.random.default_rng(11)
+    n, d, c = 20000, 8000, 50
+    a = rng.random((n, d), dtype=np.float32)
+    x = rng.random((n if trans else d, c), dtype=np.float32)
+    y = host(bk.matmul(dev(a), dev(x), trans=trans)).astype(np.float64)
+    ref = (a.astype(np.float64).T if trans else a.astype(np.float64)) @ x.astype(np.float64)
+    rel = (y - ref) / ref
+    kdim = x.shape[0]
+    assert np.max(np.abs(rel)) <= 4 * np.sqrt(kdim) * EPS[np.float32]
+    assert abs(np.mean(rel)) <= 0.5 * np.sqrt(kdim) * EPS[np.float32]   # no systematic drift
+
+
 def test_products_full_size_20000x8000():
     a, _ = synth.dense_planted_noisy()
     rng = np.random.default_rng(5)
