@@ -101,7 +101,10 @@ typedef struct {
     float ms_total;             /* ... of the whole call */
     double product_bytes;       /* algorithmic bytes moved by the A / A^T products */
     double product_flops;       /* algorithmic flops of the A / A^T products */
-    int32_t reserved[8];
+    float ms_product_kernel;    /* with opts.profile: summed event time of the tensor-core
+                                   product kernel launches alone */
+    int32_t product_kernel_launches;
+    int32_t reserved[6];
 } bks_stats;
 
 typedef struct bks_ctx bks_ctx;

@@ -45,7 +45,8 @@ class BksStats(ctypes.Structure):
         ("ms_product", ctypes.c_float), ("ms_orth", ctypes.c_float), ("ms_rr", ctypes.c_float),
         ("ms_total", ctypes.c_float),
         ("product_bytes", ctypes.c_double), ("product_flops", ctypes.c_double),
-        ("reserved", ctypes.c_int32 * 8),
+        ("ms_product_kernel", ctypes.c_float), ("product_kernel_launches", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 6),
     ]
 
     def as_dict(self):

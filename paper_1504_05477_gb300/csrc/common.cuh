@@ -31,6 +31,22 @@ template <typename T> __device__ __forceinline__ T cvt(__nv_bfloat16 x) {
 
 template <typename T> __device__ __forceinline__ bool finite_val(T x) { return isfinite(x); }
 
+// Events bracketing every launch of the dominant product kernel (profiling only).
+struct KernelLog {
+    static constexpr int CAP = 512;
+    cudaEvent_t ev[CAP];
+    int created = 0;
+    int n = 0;
+    void record(cudaStream_t s) {
+        if (n >= CAP) return;
+        if (n >= created) {
+            cudaEventCreate(&ev[n]);
+            created = n + 1;
+        }
+        cudaEventRecord(ev[n++], s);
+    }
+};
+
 // Per-call launch bookkeeping.
 struct Exec {
     cudaStream_t stream = nullptr;
@@ -38,6 +54,7 @@ struct Exec {
     int num_sms = 148;
     int launches = 0;
     int product_launches = 0;
+    KernelLog* klog = nullptr;   // non-null: time each product-kernel launch
 };
 
 // ------------------------------------------------------------------ SIMT GEMM

@@ -19,7 +19,7 @@ namespace {
 // G = R^T R with R upper triangular; Q = W R^{-1} is then Q^T = P W^T.  One CTA.
 template <typename T>
 __global__ void chol_inv_kernel(const double* __restrict__ G, int c, T* __restrict__ P,
-                                int* status, int* shifted_flag) {
+                                int* status, int* shifted_flag, bool gauss_jordan) {
     extern __shared__ unsigned char smem_raw[];
     T* S = reinterpret_cast<T*>(smem_raw);   // c*c: R (upper triangle)
     __shared__ int ok_s;
@@ -79,8 +79,33 @@ __global__ void chol_inv_kernel(const double* __restrict__ G, int c, T* __restri
         return;
     }
     if (shift > 0.0 && tid == 0) atomicOr(status, ST_SHIFTED);
-    // R^{-1} column by column: thread j solves R x = e_j by back substitution and keeps
-    // x in row j of P = R^{-T} (only thread j reads or writes that row)
+    if (gauss_jordan) {
+        // R^{-1} by Gauss-Jordan elimination on [R | I], pivots from the last row up: row i
+        // is scaled by 1/R[i][i], then column i is eliminated from the rows above.  Row i
+        // of the inverse is non-zero only in columns >= i, so each step touches i x (c-i)
+        // entries, all in parallel.
+        T* Ri = S + c * c;
+        for (int e = tid; e < c * c; e += nt) Ri[e] = T((e / c == e % c) ? 1.0 : 0.0);
+        __syncthreads();
+        const int ty = tid >> 4, tx = tid & 15;
+        for (int i = c - 1; i >= 0; --i) {
+            const T inv = T(1) / S[i * c + i];
+            for (int j = i + tid; j < c; j += nt) Ri[i * c + j] *= inv;
+            __syncthreads();
+            for (int r = ty; r < i; r += 16) {
+                const T f = S[r * c + i];
+                for (int j = i + tx; j < c; j += 16) Ri[r * c + j] -= f * Ri[i * c + j];
+            }
+            __syncthreads();
+        }
+        for (int e = tid; e < c * c; e += nt) {
+            const int a = e / c, b = e % c;
+            P[e] = Ri[b * c + a];   // P = R^{-T}
+        }
+        return;
+    }
+    // (wide FP64 blocks) R^{-1} column by column: thread j solves R x = e_j by back
+    // substitution and keeps x in row j of P = R^{-T} (only thread j touches that row)
     for (int j = tid; j < c; j += nt) {
         T* x = P + int64_t(j) * c;
         for (int i = j + 1; i < c; ++i) x[i] = T(0);
@@ -103,10 +128,11 @@ void cholqr_pass(Exec& ex, int64_t len, int64_t ld, const T* src, int c, T* dst,
     g.out = gram; g.ldo = c; g.out_transposed = false; g.out_f64 = true;
     g.alpha = 1.0; g.beta = 0.0;
     gemm_simt<T>(ex, g, partials, cap);
-    const size_t smem = size_t(c) * c * sizeof(T);
+    const bool gj = size_t(2) * c * c * sizeof(T) <= 200 * 1024;
+    const size_t smem = size_t(gj ? 2 : 1) * c * c * sizeof(T);
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(chol_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    chol_inv_kernel<T><<<1, 256, smem, ex.stream>>>(gram, c, rfac, ex.status, shifted_flag);
+    chol_inv_kernel<T><<<1, 256, smem, ex.stream>>>(gram, c, rfac, ex.status, shifted_flag, gj);
     ex.launches++;
     GemmDesc ga{};   // dst^T = P src^T: row a of dst = sum_b P[a][b] row b of src
     ga.M = c; ga.N = len; ga.K = c;

@@ -29,6 +29,10 @@ struct bks_ctx {
     int* host_status = nullptr;   // pinned: [status, sweeps, shifted]
     std::string last_error;
     std::vector<cudaEvent_t> events;
+    KernelLog klog;
+    ~bks_ctx() {
+        for (int i = 0; i < klog.created; ++i) cudaEventDestroy(klog.ev[i]);
+    }
 };
 
 namespace {
@@ -307,6 +311,10 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
     ex.stream = ctx->stream;
     ex.status = stat;
     ex.num_sms = ctx->num_sms;
+    if (o.profile) {
+        ctx->klog.n = 0;
+        ex.klog = &ctx->klog;
+    }
     Prof prof(ctx, o.profile != 0);
     const int t_all = prof.begin();
     cudaMemsetAsync(stat, 0, 4 * sizeof(int), ctx->stream);
@@ -427,6 +435,14 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
             st->ms_orth = prof.total(1);
             st->ms_rr = prof.total(2);
             st->ms_total = prof.total(3);
+            float kms = 0.f;
+            for (int i = 0; i + 1 < ctx->klog.n; i += 2) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ctx->klog.ev[i], ctx->klog.ev[i + 1]);
+                kms += ms;
+            }
+            st->ms_product_kernel = kms;
+            st->product_kernel_launches = ctx->klog.n / 2;
         }
     }
     if (status & ST_NONFINITE) return fail(ctx, BKS_ERR_NONFINITE, "non-finite value in a Gram matrix or M");

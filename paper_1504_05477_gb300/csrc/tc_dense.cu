@@ -443,24 +443,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // Tiles cut between CTAs: out[j][t*BM + m] = sum over the covering CTAs, in CTA order.
 // The CTA owning unit u is floor(((u + 1) G - 1) / U) for the ranges of unit_range.
 __global__ void tc_fixup_kernel(Params p, int G) {
+    // block (t, column group): 128 rows x 8 columns; every output is an independent sum
     const int64_t t = blockIdx.x;
-    const int m = threadIdx.x;
     const int64_t U = p.tiles * p.cpt;
     const int64_t u0 = t * p.cpt, u1 = (t + 1) * p.cpt - 1;
     const int64_t c_first = ((u0 + 1) * G - 1) / U, c_last = ((u1 + 1) * G - 1) / U;
     if (c_first == c_last) return;   // one CTA wrote the whole tile
+    const int m = threadIdx.x & (BM - 1);
+    const int j = int(blockIdx.y) * 8 + (threadIdx.x >> 7) * 4;   // blockDim = 256: 2 x 4 columns
     const int64_t row = t * BM + m;
     if (row >= p.rows_out) return;
-    for (int j = 0; j < p.c; ++j) {
-        float s = 0.f;
-        for (int64_t cc = c_first; cc <= c_last; ++cc) {
-            const int64_t start = (cc * U) / G;
-            if (((cc + 1) * U) / G == start) continue;   // a CTA with no units wrote nothing
-            const int64_t seg = t - start / p.cpt;
-            s += p.part[((cc * p.maxseg + seg) * p.cp + j) * BM + m];
-        }
-        p.out[int64_t(j) * p.ldo + row] = s;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t cc = c_first; cc <= c_last; ++cc) {
+        const int64_t start = (cc * U) / G;
+        if (((cc + 1) * U) / G == start) continue;   // a CTA with no units wrote nothing
+        const float* src = p.part + ((cc * p.maxseg + (t - start / p.cpt)) * p.cp) * BM + m;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (j + q < p.c) s[q] += src[int64_t(j + q) * BM];
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (j + q < p.c) p.out[int64_t(j + q) * p.ldo + row] = s[q];
 }
 
 // hi/lo split of a thin block (rows x len, row pitch ld).
@@ -579,8 +583,11 @@ bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda,
     case CPV:                                                                               \
         err = cudaFuncSetAttribute(tc_product_kernel<CPV>,                                  \
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)); \
-        if (err == cudaSuccess)                                                             \
+        if (err == cudaSuccess) {                                                           \
+            if (ex.klog) ex.klog->record(ex.stream);                                        \
             tc_product_kernel<CPV><<<Gc, NTHREADS, smem, ex.stream>>>(tmA, tmXh, tmXl, p);  \
+            if (ex.klog) ex.klog->record(ex.stream);                                        \
+        }                                                                                   \
         break;
             BKS_TC(32) BKS_TC(64) BKS_TC(96) BKS_TC(128)
 #undef BKS_TC
@@ -590,7 +597,7 @@ bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda,
             cudaGetLastError();
             return false;
         }
-        tc_fixup_kernel<<<unsigned(p.tiles), BM, 0, ex.stream>>>(p, Gc);
+        tc_fixup_kernel<<<dim3(unsigned(p.tiles), unsigned((cg + 7) / 8)), 2 * BM, 0, ex.stream>>>(p, Gc);
         ex.launches += 2;
     }
     return true;
