@@ -1,19 +1,26 @@
 // Eigen-decomposition of the small symmetric PSD matrix M = Q^T A A^T Q (Algorithms 1
 // and 2, step 5: its top singular vectors are its top eigenvectors) by one-sided
-// (Hestenes) Jacobi: X <- M, V <- I; for column pairs (p, q) with alpha = |x_p|^2,
-// beta = |x_q|^2, gamma = x_p . x_q, the plane rotation with
+// (Hestenes) Jacobi on the columns of X: for a column pair (p, q) with
+// alpha = |x_p|^2, beta = |x_q|^2, gamma = x_p . x_q, the plane rotation with
 // zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
-// c = 1 / sqrt(1 + t^2), s = c t makes x_p, x_q orthogonal; the same rotation is
-// applied to V.  At convergence X = M V has orthogonal columns, so
-// lambda_j = |x_j| and v_j is the matching eigenvector.
+// c = 1 / sqrt(1 + t^2), s = c t makes x_p, x_q orthogonal, and afterwards
+// |x_p|^2 = alpha - t gamma, |x_q|^2 = beta + t gamma.  The solver passes X = R^T with
+// R^T R = M (preconditioned Jacobi: no V is accumulated; the converged columns are
+// U Sigma with U the eigenvectors of M); for a PSD X = M the converged column norms
+// are its eigenvalues.
 //
 // Parallel ordering: the w columns are cut into 2C blocks of b columns held in the
 // shared memory of a thread-block cluster of C CTAs (two blocks per CTA).  Each round
 // a CTA orthogonalises every column of its first block against every column of its
 // second block; between rounds the blocks move round-robin (circle method) through
 // distributed shared memory, so every block pair meets once per sweep.  Pairs inside
-// a block are handled in the first round of each sweep.  The columns of a CTA's first
-// block live in registers (one column per warp) during the cross-block rounds.
+// a block are handled in the first round of each sweep.  During the cross-block
+// rounds a warp keeps one first-block column in registers.
+//
+// Two pair engines share this structure: a generic one (FP64 path) that recomputes
+// the three dot products per pair, and an FP32 one that uses paired FP32 arithmetic
+// (two lanes of data per instruction) and carries the column norms, recomputed
+// exactly at the start of every round, so each pair needs a single reduction.
 #include <cooperative_groups.h>
 
 #include "common.cuh"
@@ -24,7 +31,8 @@ namespace bks {
 
 namespace {
 
-constexpr int JW = 16;   // warps per CTA
+constexpr int JW = 16;          // warps per CTA
+constexpr int MOVE_REGS = 16;   // registers per thread per slot used to move one chunk
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -35,36 +43,12 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 // Rotation coefficients; returns false when the pair is already orthogonal to tol.
 template <typename T>
-__device__ __forceinline__ bool rot_coeffs(T alpha, T beta, T gamma, T tol, T& c, T& s) {
+__device__ __forceinline__ bool rot_coeffs(T alpha, T beta, T gamma, T tol, T& c, T& s, T& t) {
     if (gamma == T(0) || !(fabs(gamma) > tol * sqrt(alpha * beta))) return false;
     const T zeta = (beta - alpha) / (T(2) * gamma);
-    const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+    t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
     c = T(1) / sqrt(T(1) + t * t);
     s = c * t;
-    return true;
-}
-
-// Both columns in shared memory (intra-block pairs).
-template <typename T, int E>
-__device__ bool rotate_smem_pair(T* xp, T* xq, T tol, int lane) {
-    T a = 0, b = 0, g = 0;
-    T p[E], q[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        p[e] = xp[lane + 32 * e];
-        q[e] = xq[lane + 32 * e];
-        a = fma(p[e], p[e], a);
-        b = fma(q[e], q[e], b);
-        g = fma(p[e], q[e], g);
-    }
-    a = warp_sum(a); b = warp_sum(b); g = warp_sum(g);
-    T c, s;
-    if (!rot_coeffs(a, b, g, tol, c, s)) return false;
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        xp[lane + 32 * e] = c * p[e] - s * q[e];
-        xq[lane + 32 * e] = s * p[e] + c * q[e];
-    }
     return true;
 }
 
@@ -79,17 +63,230 @@ __device__ __forceinline__ void circle_pair(int P, int s, int i, int& a, int& b)
     }
 }
 
-constexpr int MOVE_REGS = 16;   // registers per thread per slot used to move one chunk
+// Per-CTA state in shared memory: two slots of b columns, WP values each.
+template <typename T>
+struct Blocks {
+    T* buf;
+    int b, WP;
+    __device__ T* col(int slot, int j) const { return buf + (size_t(slot) * b + j) * WP; }
+};
 
-// One-sided Jacobi on the columns of X (w x w; column j is row j of the input array).
-// Shared-memory layout per CTA: [slot 0..1][col 0..b)[WP].
+// Circle-method move of whole blocks between CTAs: top row t_0 stays; t_i -> top i+1
+// (t_{C-1} -> bottom C-1); b_0 -> top 1; b_i -> bottom i-1.  Incoming blocks are pulled
+// chunk by chunk through registers: read remote, cluster barrier, write local.
+template <typename T>
+__device__ void move_blocks(cg::cluster_group& cluster, T* buf, int per_slot, int* blk_id,
+                            int rank, int C, int tid) {
+    int src_rank[2] = {-1, -1}, src_slot[2] = {0, 0};
+    if (rank == 1) { src_rank[0] = 0; src_slot[0] = 1; }
+    else if (rank >= 2) { src_rank[0] = rank - 1; src_slot[0] = 0; }
+    if (rank == C - 1) { src_rank[1] = C - 1; src_slot[1] = 0; }
+    else { src_rank[1] = rank + 1; src_slot[1] = 1; }
+    int ids[2] = {0, 0};
+    const int chunk = JW * 32 * MOVE_REGS;
+    cluster.sync();
+    for (int base = 0; base < per_slot; base += chunk) {
+        T reg[2][MOVE_REGS];
+        for (int slot = 0; slot < 2; ++slot) {
+            if (src_rank[slot] < 0) continue;
+            const T* src = cluster.map_shared_rank(buf, src_rank[slot]) + size_t(src_slot[slot]) * per_slot;
+#pragma unroll
+            for (int r = 0; r < MOVE_REGS; ++r) {
+                const int e = base + tid + r * (JW * 32);
+                if (e < per_slot) reg[slot][r] = src[e];
+            }
+            if (base == 0) ids[slot] = cluster.map_shared_rank(blk_id, src_rank[slot])[src_slot[slot]];
+        }
+        cluster.sync();
+        for (int slot = 0; slot < 2; ++slot) {
+            if (src_rank[slot] < 0) continue;
+            T* dst = buf + size_t(slot) * per_slot;
+#pragma unroll
+            for (int r = 0; r < MOVE_REGS; ++r) {
+                const int e = base + tid + r * (JW * 32);
+                if (e < per_slot) dst[e] = reg[slot][r];
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (src_rank[0] >= 0) blk_id[0] = ids[0];
+        if (src_rank[1] >= 0) blk_id[1] = ids[1];
+    }
+    __syncthreads();
+}
+
+// Cluster-wide OR of "this CTA rotated during the sweep"; flags live in CTA 0 and
+// alternate between two rows so a row is cleared two sweeps before its next use.
+__device__ bool cluster_any(cg::cluster_group& cluster, int (*flags)[16], int par, int rank, int C,
+                            int tid, int mine) {
+    if (tid == 0) cluster.map_shared_rank(&flags[0][0], 0)[par * 16 + rank] = mine;
+    cluster.sync();
+    int tot = 0;
+    const int* f0 = cluster.map_shared_rank(&flags[0][0], 0);
+    for (int r = 0; r < C; ++r) tot |= f0[par * 16 + r];
+    cluster.sync();
+    if (rank == 0 && tid < 16) flags[par][tid] = 0;
+    return tot != 0;
+}
+
+// ------------------------------------------------------------ generic pair engine
 template <typename T, int E>
+struct GenericEngine {
+    static constexpr bool kNorms = false;
+    // both columns in shared memory
+    __device__ static bool pair_smem(T* xp, T* xq, T* np, T* nq, T tol, int lane) {
+        (void)np; (void)nq;
+        T a = 0, b = 0, g = 0;
+        T p[E], q[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            p[e] = xp[lane + 32 * e];
+            q[e] = xq[lane + 32 * e];
+            a = fma(p[e], p[e], a);
+            b = fma(q[e], q[e], b);
+            g = fma(p[e], q[e], g);
+        }
+        a = warp_sum(a); b = warp_sum(b); g = warp_sum(g);
+        T c, s, t;
+        if (!rot_coeffs(a, b, g, tol, c, s, t)) return false;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            xp[lane + 32 * e] = c * p[e] - s * q[e];
+            xq[lane + 32 * e] = s * p[e] + c * q[e];
+        }
+        return true;
+    }
+    struct Reg { T x[E]; T a; };
+    __device__ static void load(Reg& r, const T* xp, const T* np, int lane) {
+        (void)np;
+#pragma unroll
+        for (int e = 0; e < E; ++e) r.x[e] = xp[lane + 32 * e];
+    }
+    __device__ static void store(const Reg& r, T* xp, T* np, int lane) {
+        (void)np;
+#pragma unroll
+        for (int e = 0; e < E; ++e) xp[lane + 32 * e] = r.x[e];
+    }
+    // first column in registers, second in shared memory
+    __device__ static bool pair_reg(Reg& r, T* xq, T* nq, T tol, int lane) {
+        (void)nq;
+        T q[E];
+        T a = 0, bb = 0, g = 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            q[e] = xq[lane + 32 * e];
+            a = fma(r.x[e], r.x[e], a);
+            bb = fma(q[e], q[e], bb);
+            g = fma(r.x[e], q[e], g);
+        }
+        a = warp_sum(a); bb = warp_sum(bb); g = warp_sum(g);
+        T c, sn, t;
+        if (!rot_coeffs(a, bb, g, tol, c, sn, t)) return false;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const T p = r.x[e];
+            r.x[e] = c * p - sn * q[e];
+            xq[lane + 32 * e] = sn * p + c * q[e];
+        }
+        return true;
+    }
+};
+
+// -------------------------------------------------------- paired-FP32 pair engine
+// Lane l holds the float2 elements l + 32 i (i < E/2) of a column, i.e. the value
+// pairs (2l + 64 i, 2l + 64 i + 1): one 64-bit shared-memory access per pair.
+template <int E>
+struct F32x2Engine {
+    static constexpr bool kNorms = true;
+    static constexpr int H = E / 2;
+    __device__ static float dot(const float2* p, const float2* q) {
+        float2 g = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < H; ++i) g = __ffma2_rn(p[i], q[i], g);
+        return warp_sum(g.x + g.y);
+    }
+    __device__ static void rotate(float2* p, float2* q, float c, float s) {
+        const float2 c2 = make_float2(c, c), s2 = make_float2(s, s), ns2 = make_float2(-s, -s);
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            const float2 pi = p[i];
+            p[i] = __ffma2_rn(ns2, q[i], __fmul2_rn(c2, pi));
+            q[i] = __ffma2_rn(s2, pi, __fmul2_rn(c2, q[i]));
+        }
+    }
+    __device__ static bool pair_smem(float* xp, float* xq, float* np, float* nq, float tol, int lane) {
+        float2 p[H], q[H];
+        const float2* p2 = reinterpret_cast<const float2*>(xp);
+        const float2* q2 = reinterpret_cast<const float2*>(xq);
+#pragma unroll
+        for (int i = 0; i < H; ++i) { p[i] = p2[lane + 32 * i]; q[i] = q2[lane + 32 * i]; }
+        const float g = dot(p, q);
+        const float a = *np, b = *nq;
+        float c, s, t;
+        if (!rot_coeffs(a, b, g, tol, c, s, t)) return false;
+        rotate(p, q, c, s);
+        float2* pw = reinterpret_cast<float2*>(xp);
+        float2* qw = reinterpret_cast<float2*>(xq);
+#pragma unroll
+        for (int i = 0; i < H; ++i) { pw[lane + 32 * i] = p[i]; qw[lane + 32 * i] = q[i]; }
+        __syncwarp();
+        if (lane == 0) { *np = a - t * g; *nq = b + t * g; }
+        return true;
+    }
+    struct Reg { float2 x[H]; float a; };
+    __device__ static void load(Reg& r, const float* xp, const float* np, int lane) {
+        const float2* p2 = reinterpret_cast<const float2*>(xp);
+#pragma unroll
+        for (int i = 0; i < H; ++i) r.x[i] = p2[lane + 32 * i];
+        r.a = *np;
+    }
+    __device__ static void store(const Reg& r, float* xp, float* np, int lane) {
+        float2* p2 = reinterpret_cast<float2*>(xp);
+#pragma unroll
+        for (int i = 0; i < H; ++i) p2[lane + 32 * i] = r.x[i];
+        if (lane == 0) *np = r.a;
+    }
+    __device__ static bool pair_reg(Reg& r, float* xq, float* nq, float tol, int lane) {
+        float2 q[H];
+        const float2* q2 = reinterpret_cast<const float2*>(xq);
+#pragma unroll
+        for (int i = 0; i < H; ++i) q[i] = q2[lane + 32 * i];
+        const float g = dot(r.x, q);
+        const float b = *nq;
+        float c, s, t;
+        if (!rot_coeffs(r.a, b, g, tol, c, s, t)) return false;
+        rotate(r.x, q, c, s);
+        float2* qw = reinterpret_cast<float2*>(xq);
+#pragma unroll
+        for (int i = 0; i < H; ++i) qw[lane + 32 * i] = q[i];
+        r.a = r.a - t * g;
+        __syncwarp();
+        if (lane == 0) *nq = b + t * g;
+        return true;
+    }
+};
+
+// Exact squared norms of every column this CTA holds (one warp per column).
+template <typename T>
+__device__ void recompute_norms(const Blocks<T>& B, T* nrm2, int warp, int lane) {
+    for (int u = warp; u < 2 * B.b; u += JW) {
+        const T* x = B.col(u / B.b, u % B.b);
+        T s = 0;
+        for (int l = lane; l < B.WP; l += 32) s = fma(x[l], x[l], s);
+        s = warp_sum(s);
+        if (lane == 0) nrm2[u] = s;
+    }
+}
+
+template <typename T, int E, class Eng>
 __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
     const T* __restrict__ Xin, int64_t ldx, int w, int b, T* Xout, int64_t ldw, int max_sweeps,
     T tol, int* status, int* sweeps_out) {
     constexpr int WP = 32 * E;
     extern __shared__ unsigned char smem_raw[];
-    T* buf = reinterpret_cast<T*>(smem_raw);
+    Blocks<T> B{reinterpret_cast<T*>(smem_raw), b, WP};
+    T* nrm2 = B.buf + size_t(2) * b * WP;   // squared column norms [slot * b + j]
     __shared__ int blk_id[2];
     __shared__ int rotated_s;
     __shared__ int flags[2][16];
@@ -98,7 +295,6 @@ __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
     const int C = int(cluster.num_blocks());
     const int rank = int(cluster.block_rank());
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    auto col = [&](int slot, int j) -> T* { return buf + (size_t(slot) * b + j) * WP; };
 
     // initial placement: CTA r holds blocks 2r (slot 0) and 2r+1 (slot 1)
     if (tid == 0) {
@@ -109,7 +305,7 @@ __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
         const int blk = 2 * rank + slot;
         for (int j = 0; j < b; ++j) {
             const int gc = blk * b + j;
-            T* x = col(slot, j);
+            T* x = B.col(slot, j);
             for (int l = tid; l < WP; l += blockDim.x)
                 x[l] = (gc < w && l < w) ? Xin[int64_t(gc) * ldx + l] : T(0);
         }
@@ -120,8 +316,6 @@ __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
 
     const int P = 2 * C;               // players in the block round robin
     const int bp = b + (b & 1);        // intra-block players (even)
-    const int per_slot = b * WP;
-    const int chunk = JW * 32 * MOVE_REGS;
     int sweep = 0;
     bool converged = false;
     for (; sweep < max_sweeps && !converged; ++sweep) {
@@ -129,6 +323,10 @@ __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
         __syncthreads();
         bool any = false;
         for (int round = 0; round < P - 1; ++round) {
+            if (Eng::kNorms) {
+                recompute_norms(B, nrm2, warp, lane);
+                __syncthreads();
+            }
             if (round == 0) {
                 // intra-block pairs of both slots, once per sweep
                 for (int s = 0; s < bp - 1; ++s) {
@@ -137,110 +335,33 @@ __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
                         int a, c2;
                         circle_pair(bp, s, i, a, c2);
                         if (a >= b || c2 >= b) continue;
-                        any |= rotate_smem_pair<T, E>(col(slot, a), col(slot, c2), tol, lane);
+                        any |= Eng::pair_smem(B.col(slot, a), B.col(slot, c2), nrm2 + slot * b + a,
+                                              nrm2 + slot * b + c2, tol, lane);
                     }
                     __syncthreads();
                 }
             }
-            // cross pairs: warp keeps slot-0 column j in registers for b sub-rounds
+            // cross pairs: a warp keeps slot-0 column j in registers for b sub-rounds
             for (int j0 = 0; j0 < b; j0 += JW) {
                 const int j = j0 + warp;
                 const bool own = j < b;
-                T xr[E];
-                if (own) {
-#pragma unroll
-                    for (int e = 0; e < E; ++e) xr[e] = col(0, j)[lane + 32 * e];
-                }
+                typename Eng::Reg r;
+                if (own) Eng::load(r, B.col(0, j), nrm2 + j, lane);
                 for (int s = 0; s < b; ++s) {
                     if (own) {
-                        T* xq = col(1, (j + s) % b);
-                        T q[E];
-                        T a = 0, bb = 0, g = 0;
-#pragma unroll
-                        for (int e = 0; e < E; ++e) {
-                            q[e] = xq[lane + 32 * e];
-                            a = fma(xr[e], xr[e], a);
-                            bb = fma(q[e], q[e], bb);
-                            g = fma(xr[e], q[e], g);
-                        }
-                        a = warp_sum(a); bb = warp_sum(bb); g = warp_sum(g);
-                        T c, sn;
-                        if (rot_coeffs(a, bb, g, tol, c, sn)) {
-                            any = true;
-#pragma unroll
-                            for (int e = 0; e < E; ++e) {
-                                const T p = xr[e];
-                                xr[e] = c * p - sn * q[e];
-                                xq[lane + 32 * e] = sn * p + c * q[e];
-                            }
-                        }
+                        const int qj = (j + s) % b;
+                        any |= Eng::pair_reg(r, B.col(1, qj), nrm2 + b + qj, tol, lane);
                     }
                     __syncthreads();
                 }
-                if (own) {
-#pragma unroll
-                    for (int e = 0; e < E; ++e) col(0, j)[lane + 32 * e] = xr[e];
-                }
+                if (own) Eng::store(r, B.col(0, j), nrm2 + j, lane);
                 __syncthreads();
             }
-            if (C > 1) {
-                // circle-method move of whole blocks: top row t_0 fixed; t_i -> top i+1
-                // (t_{C-1} -> bottom C-1); b_0 -> top 1; b_i -> bottom i-1.  Incoming
-                // blocks are pulled chunk by chunk through registers: read remote,
-                // cluster barrier, write local.
-                int src_rank[2] = {-1, -1}, src_slot[2] = {0, 0};
-                if (rank == 1) { src_rank[0] = 0; src_slot[0] = 1; }
-                else if (rank >= 2) { src_rank[0] = rank - 1; src_slot[0] = 0; }
-                if (rank == C - 1) { src_rank[1] = C - 1; src_slot[1] = 0; }
-                else { src_rank[1] = rank + 1; src_slot[1] = 1; }
-                int ids[2] = {0, 0};
-                cluster.sync();
-                for (int base = 0; base < per_slot; base += chunk) {
-                    T reg[2][MOVE_REGS];
-                    for (int slot = 0; slot < 2; ++slot) {
-                        if (src_rank[slot] < 0) continue;
-                        const T* src = cluster.map_shared_rank(buf, src_rank[slot]) +
-                                       size_t(src_slot[slot]) * per_slot;
-#pragma unroll
-                        for (int r = 0; r < MOVE_REGS; ++r) {
-                            const int e = base + tid + r * (JW * 32);
-                            if (e < per_slot) reg[slot][r] = src[e];
-                        }
-                        if (base == 0) ids[slot] = cluster.map_shared_rank(blk_id, src_rank[slot])[src_slot[slot]];
-                    }
-                    cluster.sync();
-                    for (int slot = 0; slot < 2; ++slot) {
-                        if (src_rank[slot] < 0) continue;
-                        T* dst = buf + size_t(slot) * per_slot;
-#pragma unroll
-                        for (int r = 0; r < MOVE_REGS; ++r) {
-                            const int e = base + tid + r * (JW * 32);
-                            if (e < per_slot) dst[e] = reg[slot][r];
-                        }
-                    }
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    if (src_rank[0] >= 0) blk_id[0] = ids[0];
-                    if (src_rank[1] >= 0) blk_id[1] = ids[1];
-                }
-                __syncthreads();
-            }
+            if (C > 1) move_blocks(cluster, B.buf, b * WP, blk_id, rank, C, tid);
         }
-        // cluster-wide "did anybody rotate" for this sweep
         if (any) rotated_s = 1;
         __syncthreads();
-        const int par = sweep & 1;
-        if (tid == 0) cluster.map_shared_rank(&flags[0][0], 0)[par * 16 + rank] = rotated_s;
-        cluster.sync();
-        int tot = 0;
-        {
-            const int* f0 = cluster.map_shared_rank(&flags[0][0], 0);
-            for (int r = 0; r < C; ++r) tot |= f0[par * 16 + r];
-        }
-        cluster.sync();
-        if (rank == 0 && tid < 16) flags[par][tid] = 0;
-        converged = (tot == 0);
+        converged = !cluster_any(cluster, flags, sweep & 1, rank, C, tid, rotated_s);
     }
     if (!converged && tid == 0 && rank == 0) atomicOr(status, ST_NOT_CONVERGED);
     if (tid == 0 && rank == 0) *sweeps_out = sweep;
@@ -250,7 +371,7 @@ __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
         for (int j = 0; j < b; ++j) {
             const int gc = blk * b + j;
             if (gc >= w) continue;
-            const T* x = col(slot, j);
+            const T* x = B.col(slot, j);
             for (int l = tid; l < w; l += blockDim.x) Xout[int64_t(gc) * ldw + l] = x[l];
         }
     }
@@ -300,10 +421,15 @@ __global__ void eig_gather_kernel(const T* X, int64_t ldw, int w, const int* ord
 }
 
 template <typename T, int E>
+struct EngineFor { using type = GenericEngine<T, E>; };
+template <int E>
+struct EngineFor<float, E> { using type = F32x2Engine<E>; };
+
+template <typename T, int E>
 cudaError_t launch_cluster(cudaStream_t st, int C, size_t smem, const T* Xin, int64_t ldx, int w,
                            int b, T* X, int64_t ldw, int max_sweeps, T tol, int* status,
                            int* sweeps) {
-    auto kern = jacobi_cluster_kernel<T, E>;
+    auto kern = jacobi_cluster_kernel<T, E, typename EngineFor<T, E>::type>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     if (C > 8) {
@@ -328,10 +454,10 @@ cudaError_t launch_cluster(cudaStream_t st, int C, size_t smem, const T* Xin, in
 }  // namespace
 
 // Plan: cluster size C (power of two <= 16), block width b = ceil(w / 2C) and register
-// tile E (elements per lane per column, WP = 32 E >= w).  Returns false when w is too
-// large for this solver (shared memory per CTA would exceed 200 KB).
+// tile E (even: elements per lane per column, WP = 32 E >= w).  Returns false when w is
+// too large for this solver (shared memory per CTA would exceed 200 KB).
 bool jacobi_plan(int w, int elem_bytes, int& C, int& b, int& E, size_t& smem) {
-    static const int Es[] = {1, 2, 4, 8, 12, 16, 24, 32};
+    static const int Es[] = {2, 4, 8, 12, 16, 24, 32};
     E = 0;
     for (int e : Es)
         if (32 * e >= w) { E = e; break; }
@@ -340,7 +466,7 @@ bool jacobi_plan(int w, int elem_bytes, int& C, int& b, int& E, size_t& smem) {
     while (C < 16 && w / (2 * C) >= 16) C *= 2;   // about 16 columns per block
     for (;; C *= 2) {
         b = (w + 2 * C - 1) / (2 * C);
-        smem = size_t(2) * b * 32 * E * elem_bytes;
+        smem = (size_t(2) * b * 32 * E + size_t(2) * b) * elem_bytes;
         if (smem <= 200 * 1024) return true;
         if (C >= 16) return false;
     }
@@ -366,7 +492,7 @@ void sym_eig(Exec& ex, int w, const T* Xin, int64_t ldx, T* X, int64_t ldw, T* l
 #define BKS_JAC(EE) \
     case EE: err = launch_cluster<T, EE>(ex.stream, C, smem, Xin, ldx, w, b, X, ldw, max_sweeps, ttol, ex.status, sweeps_dev); break;
     switch (E) {
-        BKS_JAC(1) BKS_JAC(2) BKS_JAC(4) BKS_JAC(8) BKS_JAC(12) BKS_JAC(16) BKS_JAC(24) BKS_JAC(32)
+        BKS_JAC(2) BKS_JAC(4) BKS_JAC(8) BKS_JAC(12) BKS_JAC(16) BKS_JAC(24) BKS_JAC(32)
     }
 #undef BKS_JAC
     ex.launches++;

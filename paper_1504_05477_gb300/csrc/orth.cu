@@ -25,24 +25,38 @@ __global__ void chol_inv_kernel(const double* __restrict__ G, int c, T* __restri
     __shared__ int ok_s;
     __shared__ double trace_s;
     const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ double red[32];
+    // one coalesced pass over G: finiteness, the trace, and the upper triangle into S
     bool bad = false;
-    for (int e = tid; e < c * c; e += nt) bad |= !isfinite(G[e]);
+    double tr = 0.0;
+    for (int e = tid; e < c * c; e += nt) {
+        const double g = G[e];
+        bad |= !isfinite(g);
+        const int a = e / c, b = e - a * c;
+        if (a == b) tr += g;
+        S[e] = (a <= b) ? T(g) : T(0);
+    }
     if (__syncthreads_or(bad)) {
         if (tid == 0) atomicOr(status, ST_NONFINITE);
         for (int e = tid; e < c * c; e += nt) P[e] = T((e / c == e % c) ? 1.0 : 0.0);
         return;
     }
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    if ((tid & 31) == 0) red[tid >> 5] = tr;
+    __syncthreads();
     if (tid == 0) {
         double t = 0.0;
-        for (int j = 0; j < c; ++j) t += G[j * c + j];
+        for (int w = 0; w < (nt >> 5); ++w) t += red[w];
         trace_s = t;
     }
     __syncthreads();
     double shift = 0.0;
     for (int attempt = 0; attempt < 6; ++attempt) {
-        for (int a = 0; a < c; ++a)
-            for (int b = tid; b < c; b += nt)
-                S[a * c + b] = (a <= b) ? T(G[a * c + b] + (a == b ? shift : 0.0)) : T(0);
+        if (attempt > 0)   // rebuild S with a diagonal shift (rare path)
+            for (int e = tid; e < c * c; e += nt) {
+                const int a = e / c, b = e - a * c;
+                S[e] = (a <= b) ? T(G[e] + (a == b ? shift : 0.0)) : T(0);
+            }
         if (tid == 0) ok_s = 1;
         __syncthreads();
         for (int j = 0; j < c; ++j) {
