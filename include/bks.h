@@ -197,6 +197,34 @@ bks_status bks_orthonormalize(bks_ctx* ctx, int dtype, int64_t len, int m, int c
 bks_status bks_sym_eig(bks_ctx* ctx, int dtype, int w, const void* M, int64_t ldm,
                        void* lam, void* U, int64_t ldu);
 
+/* ---- allocation-free variant ------------------------------------------------------ */
+
+/* bks_sym_eig without any device allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they call, for
+ * example code running where cudaMalloc's implicit device synchronisation is not
+ * allowed, applications whose device memory is owned by another runtime or a fixed
+ * arena, or deployments that must not grow their footprint after start-up.
+ *
+ * Same computation and arguments as bks_sym_eig (one-sided Jacobi on a symmetric PSD
+ * w x w matrix M; lam descending, U's columns the eigenvectors), with no context: it
+ * runs on the caller's current device and on `stream` (a cudaStream_t, NULL = legacy
+ * default stream), and synchronises that stream once at the end to read its status.
+ * M, lam and U are caller-owned device buffers.
+ *
+ * All scratch lives in one statically sized device array of 5 MiB that is part of the
+ * library image: every GPU that loads the library holds it until the process exits.
+ * The limit is w <= BKS_NOALLOC_EIG_MAX_W (FP32 or FP64); larger w returns
+ * BKS_ERR_INVALID_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array, which keeps the
+ * previous call's contents (the status words are cleared at the start of each call):
+ * calls whose work overlaps on the GPU (other streams, other host threads) race on it
+ * and must be serialised by the caller.  Errors are returned as status codes only
+ * (there is no context for bks_last_error). */
+#define BKS_NOALLOC_EIG_MAX_W 512
+bks_status bks_sym_eig_noalloc(void* stream, int dtype, int w, const void* M, int64_t ldm,
+                               void* lam, void* U, int64_t ldu);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,6 +75,7 @@ SIGNATURES = {
     "bks_matmul": (_I32, [_P, ctypes.POINTER(BksMatrix), _I32, _I32, _P, _I64, _P, _I64, _I32]),
     "bks_orthonormalize": (_I32, [_P, _I32, _I64, _I32, _I32, _P, _I64, _P, _I64]),
     "bks_sym_eig": (_I32, [_P, _I32, _I32, _P, _I64, _P, _P, _I64]),
+    "bks_sym_eig_noalloc": (_I32, [_P, _I32, _I32, _P, _I64, _P, _P, _I64]),
 }
 
 _LIB = None
