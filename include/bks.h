@@ -182,6 +182,15 @@ bks_status bks_gen_pi_host(uint64_t seed, int64_t d, int k, float* out_host);
 bks_status bks_matmul(bks_ctx* ctx, const bks_matrix* A, int trans, int c,
                       const void* X, int64_t ldx, void* Y, int64_t ldy, int flags);
 
+/* CSR of A^T for a CSR matrix A (setup, once per matrix): t_row_ptr (d+1), t_col_idx
+ * (nnz, row indices of A) and t_vals (nnz), caller-allocated on the device.  Within a row
+ * of A^T the entries keep the ascending row order of A, so products through it are
+ * deterministic.  Pass the three arrays in bks_matrix.t_* to every later call on A; a
+ * CSR matrix given without them has its transpose rebuilt in the workspace on each
+ * call.  Synchronises the stream. */
+bks_status bks_csr_transpose(bks_ctx* ctx, const bks_matrix* A, int64_t* t_row_ptr,
+                             int32_t* t_col_idx, float* t_vals);
+
 /* Block orthonormalisation (Sec. 4.1/4.2 reorthonormalisation): W (len x c,
  * column-major, ldw) is projected twice against the m orthonormal columns of Qb
  * (len x m, column-major, ldq; m may be 0) and then orthonormalised by CholeskyQR2,

@@ -14,7 +14,7 @@ import ctypes
 from . import _binding as B
 from ._binding import BksError, BksMatrix, BksOpts, BksStats  # noqa: F401
 
-__all__ = ["block_krylov", "simul_iter", "matmul", "orthonormalize", "sym_eig", "gen_pi",
+__all__ = ["block_krylov", "simul_iter", "matmul", "orthonormalize", "sym_eig", "gen_pi", "CsrMatrix",
            "gen_pi_host", "Context", "context", "dense_matrix", "BksError", "lib_path"]
 
 
@@ -96,6 +96,60 @@ def dense_matrix(a) -> BksMatrix:
     return m
 
 
+class CsrMatrix:
+    """A sparse n x d matrix in CSR form on a CUDA device: row_ptr (int64, n+1), col_idx
+    (int32, sorted within rows), vals (float32).  The CSR of A^T is built once by the
+    library (bks_csr_transpose) unless transpose=False.  col_mean (d float32) makes every
+    product use the implicitly centred A - 1 mu^T."""
+
+    def __init__(self, row_ptr, col_idx, vals, shape, col_mean=None, transpose=True):
+        torch = _torch()
+        self.row_ptr = row_ptr.to(torch.int64).contiguous()
+        self.col_idx = col_idx.to(torch.int32).contiguous()
+        self.vals = vals.to(torch.float32).contiguous()
+        self.shape = (int(shape[0]), int(shape[1]))
+        self.device = self.vals.device
+        self.col_mean = col_mean.to(torch.float32).contiguous() if col_mean is not None else None
+        self.t = None
+        if transpose:
+            n, d = self.shape
+            nnz = self.vals.numel()
+            t_rp = torch.empty(d + 1, dtype=torch.int64, device=self.device)
+            t_ci = torch.empty(max(nnz, 1), dtype=torch.int32, device=self.device)
+            t_cv = torch.empty(max(nnz, 1), dtype=torch.float32, device=self.device)
+            ctx = context(self.device)
+            m = self.bks()
+            B.check(ctx.lib.bks_csr_transpose(ctx.ptr, ctypes.byref(m), ctypes.c_void_p(t_rp.data_ptr()),
+                                              ctypes.c_void_p(t_ci.data_ptr()),
+                                              ctypes.c_void_p(t_cv.data_ptr())),
+                    ctx.ptr, "bks_csr_transpose")
+            self.t = (t_rp, t_ci, t_cv)
+
+    def bks(self) -> BksMatrix:
+        m = BksMatrix()
+        m.kind = B.BKS_CSR
+        m.dtype = B.BKS_F32
+        m.n, m.d = self.shape
+        m.ld = self.shape[1]
+        m.vals = self.vals.data_ptr()
+        m.row_ptr = self.row_ptr.data_ptr()
+        m.col_idx = self.col_idx.data_ptr()
+        m.nnz = self.vals.numel()
+        if self.t is not None:
+            m.t_row_ptr, m.t_col_idx, m.t_vals = (x.data_ptr() for x in self.t)
+        if self.col_mean is not None:
+            m.col_mean = self.col_mean.data_ptr()
+        return m
+
+
+def _as_bks(a, precision="auto"):
+    """(bks_matrix, device, result dtype) for a dense tensor or a CsrMatrix."""
+    torch = _torch()
+    if isinstance(a, CsrMatrix):
+        return a.bks(), a.device, torch.float32
+    return dense_matrix(a), a.device, _out_dtype(a, precision)
+
+
 def _opts(precision="auto", basis_only=False, sign_fix=True, profile=False, jacobi_tol=0.0,
           jacobi_max_sweeps=40, refine=True, simt=False):
     o = BksOpts()
@@ -121,10 +175,8 @@ def _out_dtype(a, precision):
 
 def _solve(fn_name, a, k, q, seed, pi, want_v, precision, stats, **kw):
     torch = _torch()
-    mat = a if isinstance(a, BksMatrix) else dense_matrix(a)
-    dev = a.device if not isinstance(a, BksMatrix) else torch.device("cuda", kw.pop("device", 0))
+    mat, dev, odt = _as_bks(a, precision)
     ctx = context(dev)
-    odt = _out_dtype(a, precision) if not isinstance(a, BksMatrix) else kw.pop("out_dtype", torch.float32)
     n, d = mat.n, mat.d
     z = torch.empty((n, k), dtype=odt, device=dev)
     sig = torch.empty((k,), dtype=odt, device=dev)
@@ -170,8 +222,8 @@ def matmul(a, x, trans=False, simt=False, exact=False):
     (rows x c) CUDA tensor; the result is (rows' x c) in x's dtype.  simt forces the
     CUDA-core kernel; exact asks for the FP32-accurate split product on a BF16 A."""
     torch = _torch()
-    mat = dense_matrix(a)
-    ctx = context(a.device)
+    mat, dev, _ = _as_bks(a)
+    ctx = context(dev)
     xt = _colmajor(x)
     rows_y = mat.d if trans else mat.n
     yt = torch.empty((x.shape[1], rows_y), dtype=x.dtype, device=x.device)

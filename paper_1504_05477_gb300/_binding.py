@@ -72,6 +72,7 @@ SIGNATURES = {
                               ctypes.POINTER(BksOpts), ctypes.POINTER(BksStats)]),
     "bks_gen_pi": (_I32, [_P, _U64, _I64, _I32, _I32, _P]),
     "bks_gen_pi_host": (_I32, [_U64, _I64, _I32, ctypes.POINTER(ctypes.c_float)]),
+    "bks_csr_transpose": (_I32, [_P, ctypes.POINTER(BksMatrix), _P, _P, _P]),
     "bks_matmul": (_I32, [_P, ctypes.POINTER(BksMatrix), _I32, _I32, _P, _I64, _P, _I64, _I32]),
     "bks_orthonormalize": (_I32, [_P, _I32, _I64, _I32, _I32, _P, _I64, _P, _I64]),
     "bks_sym_eig": (_I32, [_P, _I32, _I32, _P, _I64, _P, _P, _I64]),

@@ -93,6 +93,22 @@ bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda,
                     float* part, int64_t part_cap);
 int64_t tc_partial_floats(int64_t n, int64_t d, int c, int num_sms);
 
+// ------------------------------------------------------------------ sparse A (CSR)
+size_t csr_transpose_scratch(int64_t n, int64_t d);
+// CSR of A^T (rows of A^T in ascending row order of A: deterministic).
+void csr_transpose(Exec& ex, const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n,
+                   int64_t d, int64_t nnz, int64_t* t_row_ptr, int32_t* t_col, float* t_val,
+                   void* scratch);
+int64_t seg_upper_bound(int64_t rows, int64_t nnz);
+void csr_segments(Exec& ex, const int64_t* row_ptr, int64_t rows, int64_t* nseg_tmp, int64_t* seg_off,
+                  int64_t* seg_row, int64_t* sums);
+// Yt (c x ldy thin) = op(A) Xt with op(A) given by its CSR (rows x cols); corr_kind 0: none,
+// 1: subtract mu^T X from every row, 2: subtract mu[row] (1^T X).
+void csr_product(Exec& ex, const int64_t* row_ptr, const int32_t* col, const float* val, int64_t rows,
+                 int64_t cols, int64_t nnz, const int64_t* seg_off, const int64_t* seg_row,
+                 int64_t nseg_bound, const float* Xt, int64_t ldx, int c, float* Yt, int64_t ldy,
+                 float* x_rm, float* y_rm, float* part, int corr_kind, const float* mu, double* cvec);
+
 // ------------------------------------------------------------------ building blocks
 template <typename T>
 void gen_pi_device(Exec& ex, uint64_t seed, int64_t d, int k, T* out, int64_t ld_row,

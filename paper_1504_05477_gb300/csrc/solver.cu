@@ -107,9 +107,32 @@ bks_status check_matrix(bks_ctx* ctx, const bks_matrix* A) {
             return fail(ctx, BKS_ERR_UNSUPPORTED, "implicit centring is implemented for CSR A only");
         return BKS_OK;
     }
-    if (A->kind == BKS_CSR) return fail(ctx, BKS_ERR_UNSUPPORTED, "CSR A is not built yet");
+    if (A->kind == BKS_CSR) {
+        if (A->dtype != BKS_F32) return fail(ctx, BKS_ERR_UNSUPPORTED, "CSR values must be FP32");
+        if (A->row_ptr == nullptr || A->col_idx == nullptr || A->vals == nullptr || A->nnz < 0)
+            return fail(ctx, BKS_ERR_INVALID_ARG, "CSR arrays missing");
+        const bool tr = A->t_row_ptr != nullptr, tc = A->t_col_idx != nullptr, tv = A->t_vals != nullptr;
+        if (tr != tc || tc != tv)
+            return fail(ctx, BKS_ERR_INVALID_ARG, "give all three arrays of the CSR of A^T or none");
+        return BKS_OK;
+    }
     return fail(ctx, BKS_ERR_INVALID_ARG, "unknown matrix kind");
 }
+
+// Scratch of the sparse products: segment plans of A and A^T (index 0 and 1), the CSR
+// of A^T when the caller did not give it, row-major staging of X and Y, partial sums.
+struct CsrWs {
+    const int64_t* rp[2] = {nullptr, nullptr};
+    const int32_t* ci[2] = {nullptr, nullptr};
+    const float* cv[2] = {nullptr, nullptr};
+    int64_t* seg_off[2] = {nullptr, nullptr};
+    int64_t* seg_row[2] = {nullptr, nullptr};
+    int64_t segb[2] = {0, 0};
+    float* x_rm = nullptr;
+    float* y_rm = nullptr;
+    float* part = nullptr;
+    double* cvec = nullptr;
+};
 
 // Scratch of the tensor-core product: hi/lo split of X and partial tiles.
 struct ProductWs {
@@ -118,6 +141,72 @@ struct ProductWs {
     float* tpart = nullptr;
     int64_t tpart_cap = 0;
     bool simt_only = false;
+    CsrWs csr;
+};
+
+// Workspace layout of the sparse machinery for c columns; `build` also lays out room
+// for the CSR of A^T and the transpose scratch when the caller did not give it.
+struct CsrLayout {
+    size_t seg_off0, seg_row0, seg_off1, seg_row1, nseg_tmp, sums, x_rm, y_rm, part, cvec;
+    size_t t_rp, t_ci, t_cv, tscratch;
+    int64_t segb0, segb1;
+    bool build;
+    void take(Arena& a, const bks_matrix* A, int c) {
+        const int64_t n = A->n, d = A->d, nnz = A->nnz, mx = n > d ? n : d;
+        segb0 = seg_upper_bound(n, nnz);
+        segb1 = seg_upper_bound(d, nnz);
+        seg_off0 = a.take(size_t(n + 1) * 8);
+        seg_row0 = a.take(size_t(segb0) * 8);
+        seg_off1 = a.take(size_t(d + 1) * 8);
+        seg_row1 = a.take(size_t(segb1) * 8);
+        nseg_tmp = a.take(size_t(mx + 1) * 8);
+        sums = a.take(size_t(mx / 1024 + 4) * 8);
+        x_rm = a.take(size_t(mx) * c * 4);
+        y_rm = a.take(size_t(mx) * c * 4);
+        part = a.take(size_t(segb0 > segb1 ? segb0 : segb1) * c * 4);
+        cvec = a.take(size_t(c) * 8);
+        build = A->t_row_ptr == nullptr;
+        if (build) {
+            t_rp = a.take(size_t(d + 1) * 8);
+            t_ci = a.take(size_t(nnz) * 4 + 16);
+            t_cv = a.take(size_t(nnz) * 4 + 16);
+            tscratch = a.take(csr_transpose_scratch(n, d));
+        }
+    }
+    // Build the CSR of A^T if needed and both segment plans; fill ws.
+    void prepare(Exec& ex, char* base, const bks_matrix* A, CsrWs& ws) const {
+        ws.rp[0] = A->row_ptr;
+        ws.ci[0] = A->col_idx;
+        ws.cv[0] = static_cast<const float*>(A->vals);
+        if (build) {
+            int64_t* trp = reinterpret_cast<int64_t*>(base + t_rp);
+            int32_t* tci = reinterpret_cast<int32_t*>(base + t_ci);
+            float* tcv = reinterpret_cast<float*>(base + t_cv);
+            csr_transpose(ex, A->row_ptr, A->col_idx, static_cast<const float*>(A->vals), A->n, A->d,
+                          A->nnz, trp, tci, tcv, base + tscratch);
+            ws.rp[1] = trp;
+            ws.ci[1] = tci;
+            ws.cv[1] = tcv;
+        } else {
+            ws.rp[1] = A->t_row_ptr;
+            ws.ci[1] = A->t_col_idx;
+            ws.cv[1] = static_cast<const float*>(A->t_vals);
+        }
+        ws.seg_off[0] = reinterpret_cast<int64_t*>(base + seg_off0);
+        ws.seg_row[0] = reinterpret_cast<int64_t*>(base + seg_row0);
+        ws.seg_off[1] = reinterpret_cast<int64_t*>(base + seg_off1);
+        ws.seg_row[1] = reinterpret_cast<int64_t*>(base + seg_row1);
+        ws.segb[0] = segb0;
+        ws.segb[1] = segb1;
+        int64_t* tmp = reinterpret_cast<int64_t*>(base + nseg_tmp);
+        int64_t* sm = reinterpret_cast<int64_t*>(base + sums);
+        csr_segments(ex, ws.rp[0], A->n, tmp, ws.seg_off[0], ws.seg_row[0], sm);
+        csr_segments(ex, ws.rp[1], A->d, tmp, ws.seg_off[1], ws.seg_row[1], sm);
+        ws.x_rm = reinterpret_cast<float*>(base + x_rm);
+        ws.y_rm = reinterpret_cast<float*>(base + y_rm);
+        ws.part = reinterpret_cast<float*>(base + part);
+        ws.cvec = reinterpret_cast<double*>(base + cvec);
+    }
 };
 
 // Products with A, in precision T: the tcgen05 kernel for an FP32 dense A when the
@@ -125,6 +214,17 @@ struct ProductWs {
 template <typename T>
 void product(Exec& ex, const bks_matrix* A, bool trans, int c, const T* X, int64_t ldx, T* Y,
              int64_t ldy, double* part, int64_t cap, const ProductWs& pw) {
+    if (A->kind == BKS_CSR) {   // FP32 only (checked on entry)
+        const int s = trans ? 1 : 0;
+        const int before = ex.launches;
+        const CsrWs& w = pw.csr;
+        csr_product(ex, w.rp[s], w.ci[s], w.cv[s], trans ? A->d : A->n, trans ? A->n : A->d, A->nnz,
+                    w.seg_off[s], w.seg_row[s], w.segb[s], reinterpret_cast<const float*>(X), ldx, c,
+                    reinterpret_cast<float*>(Y), ldy, w.x_rm, w.y_rm, w.part,
+                    A->col_mean ? (trans ? 2 : 1) : 0, A->col_mean, w.cvec);
+        ex.product_launches += ex.launches - before;
+        return;
+    }
     if (sizeof(T) == 4 && A->dtype == BKS_F32 && !pw.simt_only && pw.xh != nullptr) {
         const int before = ex.launches;
         if (tc_product_f32(ex, static_cast<const float*>(A->vals), A->n, A->d, A->ld, trans, c,
@@ -155,6 +255,8 @@ struct Plan {
     int k, q, w;
     size_t xh, xl, tpart;
     int64_t tpart_cap;
+    bool sparse;
+    CsrLayout csr;
     size_t Qt, Bt, QBt, Pit, W, Wtmp, Wb, Wbtmp, part, gram, rfac, ct, Rm, JX, lam, nrm, Vt,
         order, Vk, stat;
     int64_t part_cap;
@@ -180,7 +282,8 @@ int64_t max_partials(int64_t n, int64_t d, int k, int w, int sms) {
     return p;
 }
 
-Plan make_plan(int64_t n, int64_t d, int k, int q_eff, int w, size_t tb, int sms) {
+Plan make_plan(const bks_matrix* A, int k, int q_eff, int w, size_t tb, int sms) {
+    const int64_t n = A->n, d = A->d;
     Plan p{};
     p.n = n; p.d = d; p.k = k; p.q = q_eff; p.w = w;
     p.ldn = round_up(n, 32);
@@ -212,6 +315,8 @@ Plan make_plan(int64_t n, int64_t d, int k, int q_eff, int w, size_t tb, int sms
     p.tpart_cap = tc_partial_floats(n, d, k, sms);
     p.tpart = a.take(size_t(p.tpart_cap) * 4);
     p.stat = a.take(4 * sizeof(int));
+    p.sparse = A->kind == BKS_CSR;
+    if (p.sparse) p.csr.take(a, A, k);
     p.total = a.off;
     return p;
 }
@@ -273,7 +378,7 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
             return fail(ctx, BKS_ERR_UNSUPPORTED,
                         "Krylov width " + std::to_string(w) + " exceeds the Jacobi solver's limit");
     }
-    Plan p = make_plan(n, d, k, q_eff, w, sizeof(T), ctx->num_sms);
+    Plan p = make_plan(A, k, q_eff, w, sizeof(T), ctx->num_sms);
     bks_status s = ensure_ws(ctx, p.total);
     if (s != BKS_OK) return s;
     char* base = static_cast<char*>(ctx->ws);
@@ -318,6 +423,7 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
     Prof prof(ctx, o.profile != 0);
     const int t_all = prof.begin();
     cudaMemsetAsync(stat, 0, 4 * sizeof(int), ctx->stream);
+    if (p.sparse) p.csr.prepare(ex, base, A, pw.csr);   // segment plans (+ CSR of A^T)
 
     // a0: start block, stored transposed (k x ldd)
     if (pi != nullptr)
@@ -427,7 +533,9 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
         st->launches = ex.launches;
         st->product_launches = ex.product_launches;
         const int nprod = krylov ? 2 * q_eff + 2 : 2 * q_eff + 2;
-        const double abytes = double(n) * double(A->ld) * double(dtype_bytes(A->dtype));
+        const double abytes = A->kind == BKS_CSR
+                                  ? double(A->nnz) * 8.0 + double(n + 1) * 8.0   // values + indices + offsets
+                                  : double(n) * double(A->ld) * double(dtype_bytes(A->dtype));
         st->product_bytes = nprod * (abytes + double(k) * (n + d) * sizeof(T));
         st->product_flops = nprod * 2.0 * double(n) * double(d) * k;
         if (o.profile) {
@@ -473,6 +581,8 @@ bks_status solve_entry(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t
     if (prec == BKS_PREC_BF16) return fail(ctx, BKS_ERR_UNSUPPORTED, "BF16 precision mode is not built yet");
     if (prec != BKS_PREC_F64 && prec != BKS_PREC_F32) return fail(ctx, BKS_ERR_INVALID_ARG, "bad precision");
     DeviceGuard g(ctx->device);
+    if (A->kind == BKS_CSR && prec != BKS_PREC_F32)
+        return fail(ctx, BKS_ERR_UNSUPPORTED, "a CSR matrix is solved on the FP32 path");
     if (prec == BKS_PREC_F64) return solve<double>(ctx, A, k, q, seed, pi, Z, sigma, V, o, st, krylov);
     return solve<float>(ctx, A, k, q, seed, pi, Z, sigma, V, o, st, krylov);
 }
@@ -589,7 +699,7 @@ bks_status bks_workspace_size(const bks_matrix* A, int k, int q, int method, con
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaGetLastError();
-    *bytes = make_plan(A->n, A->d, k, q_eff, w, tb, sms).total;
+    *bytes = make_plan(A, k, q_eff, w, tb, sms).total;
     return BKS_OK;
 }
 
@@ -625,6 +735,26 @@ bks_status bks_gen_pi_host(uint64_t seed, int64_t d, int k, float* out_host) {
     return BKS_OK;
 }
 
+bks_status bks_csr_transpose(bks_ctx* ctx, const bks_matrix* A, int64_t* t_row_ptr,
+                             int32_t* t_col_idx, float* t_vals) {
+    if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
+    bks_status s = check_matrix(ctx, A);
+    if (s != BKS_OK) return s;
+    if (A->kind != BKS_CSR || t_row_ptr == nullptr || t_col_idx == nullptr || t_vals == nullptr)
+        return fail(ctx, BKS_ERR_INVALID_ARG, "bks_csr_transpose needs a CSR matrix and three outputs");
+    DeviceGuard g(ctx->device);
+    s = ensure_ws(ctx, csr_transpose_scratch(A->n, A->d) + 256);
+    if (s != BKS_OK) return s;
+    Exec ex;
+    ex.stream = ctx->stream;
+    ex.num_sms = ctx->num_sms;
+    csr_transpose(ex, A->row_ptr, A->col_idx, static_cast<const float*>(A->vals), A->n, A->d, A->nnz,
+                  t_row_ptr, t_col_idx, t_vals, ctx->ws);
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e == cudaSuccess ? BKS_OK : cuda_fail(ctx, e, "bks_csr_transpose");
+}
+
 bks_status bks_matmul(bks_ctx* ctx, const bks_matrix* A, int trans, int c, const void* X,
                       int64_t ldx, void* Y, int64_t ldy, int flags) {
     if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
@@ -641,6 +771,8 @@ bks_status bks_matmul(bks_ctx* ctx, const bks_matrix* A, int trans, int c, const
     const size_t o_part = ar.take(size_t(cap) * sizeof(double) + 8),
                  o_xh = ar.take(size_t(c) * ldx * 4), o_xl = ar.take(size_t(c) * ldx * 4),
                  o_tp = ar.take(size_t(tcap) * 4), o_stat = ar.take(16);
+    CsrLayout cl{};
+    if (A->kind == BKS_CSR) cl.take(ar, A, c);
     s = ensure_ws(ctx, ar.off);
     if (s != BKS_OK) return s;
     Exec ex;
@@ -657,6 +789,7 @@ bks_status bks_matmul(bks_ctx* ctx, const bks_matrix* A, int trans, int c, const
     int* stat = reinterpret_cast<int*>(wsb + o_stat);
     ex.status = stat;
     cudaMemsetAsync(stat, 0, 16, ctx->stream);
+    if (A->kind == BKS_CSR) cl.prepare(ex, wsb, A, pw.csr);
     if (f64)
         product<double>(ex, A, trans != 0, c, static_cast<const double*>(X), ldx,
                         static_cast<double*>(Y), ldy, part, cap, pw);
