@@ -18,6 +18,7 @@ enum : int {
     ST_NOT_CONVERGED = 4,
     ST_TIMEOUT = 8,
     ST_SHIFTED = 16,
+    ST_BADINPUT = 32,     // a CSR structure check failed (nothing indexed through it)
 };
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -95,6 +96,12 @@ int64_t tc_partial_floats(int64_t n, int64_t d, int c, int num_sms);
 
 // ------------------------------------------------------------------ sparse A (CSR)
 size_t csr_transpose_scratch(int64_t n, int64_t d);
+// Structure check of a CSR (rows x cols): row_ptr[0] = 0, non-decreasing, row_ptr[rows] =
+// nnz, column indices in [0, cols) and strictly increasing within each row.  A failure
+// ORs ST_BADINPUT into *status; every later CSR kernel of the call reads *status and
+// then indexes nothing through the arrays.
+void csr_check(Exec& ex, const int64_t* row_ptr, const int32_t* col, int64_t rows, int64_t cols,
+               int64_t nnz, int* status);
 // CSR of A^T (rows of A^T in ascending row order of A: deterministic).
 void csr_transpose(Exec& ex, const int64_t* row_ptr, const int32_t* col, const float* val, int64_t n,
                    int64_t d, int64_t nnz, int64_t* t_row_ptr, int32_t* t_col, float* t_val,

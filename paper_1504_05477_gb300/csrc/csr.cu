@@ -62,8 +62,41 @@ __global__ void scan_apply(const int64_t* in, int64_t n, const int64_t* sums, in
     if (i == n - 1) out[n] = sums[blockIdx.x] + s[threadIdx.x];
 }
 
+// ------------------------------------------------------------------ structure check
+__device__ __forceinline__ bool bad_input(const int* status) {
+    return (*reinterpret_cast<const volatile int*>(status) & ST_BADINPUT) != 0;
+}
+
+__global__ void csr_check_ptr(const int64_t* row_ptr, int64_t rows, int64_t nnz, int* status) {
+    for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r <= rows;
+         r += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t v = row_ptr[r];
+        bool bad = v < 0 || v > nnz || (r == 0 && v != 0) || (r == rows && v != nnz);
+        if (r < rows && row_ptr[r + 1] < v) bad = true;
+        if (bad) atomicOr(status, ST_BADINPUT);
+    }
+}
+
+// One warp per row; runs only when the row pointers passed.
+__global__ void csr_check_cols(const int64_t* row_ptr, const int32_t* col, int64_t rows, int64_t cols,
+                               int* status) {
+    if (bad_input(status)) return;
+    const int lane = threadIdx.x & 31;
+    bool bad = false;
+    for (int64_t r = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; r < rows;
+         r += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+        const int64_t b = row_ptr[r], e = row_ptr[r + 1];
+        for (int64_t p = b + lane; p < e; p += 32) {
+            const int32_t c = col[p];
+            if (c < 0 || c >= cols || (p > b && col[p - 1] >= c)) bad = true;
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_BADINPUT);
+}
+
 // ------------------------------------------------------------------ transpose
-__global__ void col_counts(const int32_t* col, int64_t nnz, int64_t* cnt) {
+__global__ void col_counts(const int32_t* col, int64_t nnz, int64_t* cnt, const int* status) {
+    if (bad_input(status)) return;
     for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < nnz;
          p += int64_t(gridDim.x) * blockDim.x)
         atomicAdd(reinterpret_cast<unsigned long long*>(&cnt[col[p]]), 1ull);
@@ -71,7 +104,8 @@ __global__ void col_counts(const int32_t* col, int64_t nnz, int64_t* cnt) {
 
 // Per row-block column counts: bc[b * d + c] (int32), rows [b*RB, (b+1)*RB).
 __global__ void block_col_counts(const int64_t* row_ptr, const int32_t* col, int64_t n, int64_t d,
-                                 int rb, int* bc) {
+                                 int rb, int* bc, const int* status) {
+    if (bad_input(status)) return;
     const int64_t b = blockIdx.x;
     const int64_t r0 = b * rb, r1 = min(n, r0 + rb);
     for (int64_t p = row_ptr[r0] + threadIdx.x; p < row_ptr[r1]; p += blockDim.x)
@@ -96,7 +130,8 @@ __global__ void block_col_offsets(int* bc, const int64_t* t_row_ptr, int64_t d, 
 // lanes of a step never share a counter: entries land in ascending row order.
 __global__ void ordered_scatter(const int64_t* row_ptr, const int32_t* col, const float* val,
                                 int64_t n, int64_t d, int rb, int64_t nblocks, int64_t* boff,
-                                int32_t* t_col, float* t_val) {
+                                int32_t* t_col, float* t_val, const int* status) {
+    if (bad_input(status)) return;
     const int64_t b = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (b >= nblocks) return;
@@ -115,10 +150,12 @@ __global__ void ordered_scatter(const int64_t* row_ptr, const int32_t* col, cons
 }
 
 // ------------------------------------------------------------------ segments
-__global__ void seg_counts(const int64_t* row_ptr, int64_t rows, int64_t* nseg) {
+// After a failed structure check every row gets one segment (a plan that stays in bounds).
+__global__ void seg_counts(const int64_t* row_ptr, int64_t rows, int64_t* nseg, const int* status) {
+    const bool bad = bad_input(status);
     for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < rows;
          r += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t len = row_ptr[r + 1] - row_ptr[r];
+        const int64_t len = bad ? 0 : row_ptr[r + 1] - row_ptr[r];
         nseg[r] = len <= SEG ? 1 : (len + SEG - 1) / SEG;
     }
 }
@@ -138,7 +175,9 @@ __global__ void spmm_seg_kernel(const int64_t* __restrict__ row_ptr, const int32
                                 const float* __restrict__ val, const int64_t* __restrict__ seg_off,
                                 const int64_t* __restrict__ seg_row, int64_t rows, const float* __restrict__ X,
                                 int c, float* __restrict__ out, float* __restrict__ part, int corr_kind,
-                                const double* __restrict__ cvec, const float* __restrict__ mu) {
+                                const double* __restrict__ cvec, const float* __restrict__ mu,
+                                const int* status) {
+    if (bad_input(status)) return;
     const int lane = threadIdx.x & 31;
     const int64_t nseg = seg_off[rows];   // segments actually planned
     for (int64_t s = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; s < nseg;
@@ -232,6 +271,13 @@ int grid_for(int64_t work, int per_block, int num_sms) {
 }  // namespace
 
 // ---------------------------------------------------------------------- public pieces
+void csr_check(Exec& ex, const int64_t* row_ptr, const int32_t* col, int64_t rows, int64_t cols,
+               int64_t nnz, int* status) {
+    csr_check_ptr<<<grid_for(rows + 1, 256, ex.num_sms), 256, 0, ex.stream>>>(row_ptr, rows, nnz, status);
+    csr_check_cols<<<grid_for(rows, 8, ex.num_sms), 256, 0, ex.stream>>>(row_ptr, col, rows, cols, status);
+    ex.launches += 2;
+}
+
 size_t csr_transpose_scratch(int64_t n, int64_t d) {
     const int rb = 512;
     const int64_t nb = (n + rb - 1) / rb;
@@ -251,12 +297,12 @@ void csr_transpose(Exec& ex, const int64_t* row_ptr, const int32_t* col, const f
     boff = reinterpret_cast<int64_t*>((reinterpret_cast<uintptr_t>(boff) + 7) & ~uintptr_t(7));
     cudaMemsetAsync(cnt, 0, size_t(d + 1) * 8, ex.stream);
     cudaMemsetAsync(bc, 0, size_t(nb) * d * 4, ex.stream);
-    col_counts<<<grid_for(nnz, 256, ex.num_sms), 256, 0, ex.stream>>>(col, nnz, cnt);
+    col_counts<<<grid_for(nnz, 256, ex.num_sms), 256, 0, ex.stream>>>(col, nnz, cnt, ex.status);
     exclusive_scan(ex, cnt, d, t_row_ptr, sums);
-    block_col_counts<<<unsigned(nb), 256, 0, ex.stream>>>(row_ptr, col, n, d, rb, bc);
+    block_col_counts<<<unsigned(nb), 256, 0, ex.stream>>>(row_ptr, col, n, d, rb, bc, ex.status);
     block_col_offsets<<<grid_for(d, 256, ex.num_sms), 256, 0, ex.stream>>>(bc, t_row_ptr, d, nb, boff);
     ordered_scatter<<<unsigned((nb * 32 + 255) / 256), 256, 0, ex.stream>>>(row_ptr, col, val, n, d, rb, nb,
-                                                                            boff, t_col, t_val);
+                                                                            boff, t_col, t_val, ex.status);
     ex.launches += 4;
 }
 
@@ -266,7 +312,7 @@ int64_t seg_upper_bound(int64_t rows, int64_t nnz) { return rows + nnz / SEG + 1
 
 void csr_segments(Exec& ex, const int64_t* row_ptr, int64_t rows, int64_t* nseg_tmp, int64_t* seg_off,
                   int64_t* seg_row, int64_t* sums) {
-    seg_counts<<<grid_for(rows, 256, ex.num_sms), 256, 0, ex.stream>>>(row_ptr, rows, nseg_tmp);
+    seg_counts<<<grid_for(rows, 256, ex.num_sms), 256, 0, ex.stream>>>(row_ptr, rows, nseg_tmp, ex.status);
     exclusive_scan(ex, nseg_tmp, rows, seg_off, sums);
     seg_fill<<<grid_for(rows, 256, ex.num_sms), 256, 0, ex.stream>>>(row_ptr, rows, seg_off, seg_row);
     ex.launches += 2;
@@ -290,7 +336,7 @@ void csr_product(Exec& ex, const int64_t* row_ptr, const int32_t* col, const flo
     }
     const int warps_per_block = 8;
     spmm_seg_kernel<<<grid_for(nseg_bound, warps_per_block, ex.num_sms), 32 * warps_per_block, 0, ex.stream>>>(
-        row_ptr, col, val, seg_off, seg_row, rows, x_rm, c, y_rm, part, corr_kind, cvec, mu);
+        row_ptr, col, val, seg_off, seg_row, rows, x_rm, c, y_rm, part, corr_kind, cvec, mu, ex.status);
     spmm_fixup_kernel<<<grid_for(rows * c, 256, ex.num_sms), 256, 0, ex.stream>>>(seg_off, rows, part, c, y_rm,
                                                                                  corr_kind, cvec, mu);
     transpose_in<float>(ex, y_rm, 1, rows, c, c, Yt, ldy);   // Yt[j][r] = y_rm[r][j]

@@ -178,6 +178,8 @@ struct CsrLayout {
         ws.rp[0] = A->row_ptr;
         ws.ci[0] = A->col_idx;
         ws.cv[0] = static_cast<const float*>(A->vals);
+        csr_check(ex, A->row_ptr, A->col_idx, A->n, A->d, A->nnz, ex.status);
+        if (!build) csr_check(ex, A->t_row_ptr, A->t_col_idx, A->d, A->n, A->nnz, ex.status);
         if (build) {
             int64_t* trp = reinterpret_cast<int64_t*>(base + t_rp);
             int32_t* tci = reinterpret_cast<int32_t*>(base + t_ci);
@@ -532,12 +534,15 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
         st->chol_shifts = ctx->host_status[2];
         st->launches = ex.launches;
         st->product_launches = ex.product_launches;
-        const int nprod = krylov ? 2 * q_eff + 2 : 2 * q_eff + 2;
+        const int nprod = 2 * q_eff + 2;   // q+1 products with A, q+1 with A^T (both methods)
+        // A once per product (CSR: values + column indices, and the row offsets of A or of
+        // A^T, averaged), the thin input read once and the thin output written once.
         const double abytes = A->kind == BKS_CSR
-                                  ? double(A->nnz) * 8.0 + double(n + 1) * 8.0   // values + indices + offsets
+                                  ? double(A->nnz) * 8.0 + double(n + d + 2) * 4.0
                                   : double(n) * double(A->ld) * double(dtype_bytes(A->dtype));
         st->product_bytes = nprod * (abytes + double(k) * (n + d) * sizeof(T));
-        st->product_flops = nprod * 2.0 * double(n) * double(d) * k;
+        st->product_flops = nprod * 2.0 * k *
+                            (A->kind == BKS_CSR ? double(A->nnz) : double(n) * double(d));
         if (o.profile) {
             st->ms_product = prof.total(0);
             st->ms_orth = prof.total(1);
@@ -553,6 +558,7 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
             st->product_kernel_launches = ctx->klog.n / 2;
         }
     }
+    if (status & ST_BADINPUT) return fail(ctx, BKS_ERR_INVALID_ARG, "CSR structure check failed");
     if (status & ST_NONFINITE) return fail(ctx, BKS_ERR_NONFINITE, "non-finite value in a Gram matrix or M");
     if (status & ST_BREAKDOWN) return fail(ctx, BKS_ERR_BREAKDOWN, "Cholesky breakdown after shifting");
     if (status & ST_NOT_CONVERGED) return fail(ctx, BKS_ERR_NOT_CONVERGED, "Jacobi sweep cap reached");
@@ -743,16 +749,25 @@ bks_status bks_csr_transpose(bks_ctx* ctx, const bks_matrix* A, int64_t* t_row_p
     if (A->kind != BKS_CSR || t_row_ptr == nullptr || t_col_idx == nullptr || t_vals == nullptr)
         return fail(ctx, BKS_ERR_INVALID_ARG, "bks_csr_transpose needs a CSR matrix and three outputs");
     DeviceGuard g(ctx->device);
-    s = ensure_ws(ctx, csr_transpose_scratch(A->n, A->d) + 256);
+    const size_t o_stat = round_up(int64_t(csr_transpose_scratch(A->n, A->d)), 256);
+    s = ensure_ws(ctx, o_stat + 256);
     if (s != BKS_OK) return s;
     Exec ex;
     ex.stream = ctx->stream;
     ex.num_sms = ctx->num_sms;
+    ex.status = reinterpret_cast<int*>(static_cast<char*>(ctx->ws) + o_stat);
+    cudaMemsetAsync(ex.status, 0, sizeof(int), ctx->stream);
+    csr_check(ex, A->row_ptr, A->col_idx, A->n, A->d, A->nnz, ex.status);
     csr_transpose(ex, A->row_ptr, A->col_idx, static_cast<const float*>(A->vals), A->n, A->d, A->nnz,
                   t_row_ptr, t_col_idx, t_vals, ctx->ws);
-    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    cudaError_t e = cudaMemcpyAsync(ctx->host_status, ex.status, sizeof(int), cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess) e = cudaGetLastError();
-    return e == cudaSuccess ? BKS_OK : cuda_fail(ctx, e, "bks_csr_transpose");
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bks_csr_transpose");
+    if (ctx->host_status[0] & ST_BADINPUT)
+        return fail(ctx, BKS_ERR_INVALID_ARG, "CSR structure check failed (row_ptr or col_idx)");
+    return BKS_OK;
 }
 
 bks_status bks_matmul(bks_ctx* ctx, const bks_matrix* A, int trans, int c, const void* X,
@@ -801,6 +816,7 @@ bks_status bks_matmul(bks_ctx* ctx, const bks_matrix* A, int trans, int c, const
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "bks_matmul");
+    if (ctx->host_status[0] & ST_BADINPUT) return fail(ctx, BKS_ERR_INVALID_ARG, "CSR structure check failed");
     if (ctx->host_status[0] & ST_TIMEOUT)
         return fail(ctx, BKS_ERR_TIMEOUT, "a tensor-core pipeline wait timed out");
     return BKS_OK;

@@ -137,3 +137,41 @@ def test_sparse_without_transpose_matches_with():
     _, s1 = bk.block_krylov(a1, 16, 4, pi=pi)
     _, s2 = bk.block_krylov(a2, 16, 4, pi=pi)
     assert np.array_equal(host(s1), host(s2))
+
+
+def _bad_structures():
+    """Small CSR arrays (6 x 5) with one structural defect each."""
+    rp = np.array([0, 2, 3, 3, 5, 6, 8], np.int64)
+    ci = np.array([0, 3, 1, 2, 4, 0, 1, 4], np.int32)
+    out = {}
+    dup = ci.copy(); dup[1] = 0                       # repeated column in row 0
+    out["duplicate"] = (rp, dup)
+    oob = ci.copy(); oob[4] = 5                       # column index == d
+    out["column_range"] = (rp, oob)
+    neg = ci.copy(); neg[2] = -1
+    out["negative_column"] = (rp, neg)
+    uns = ci.copy(); uns[3], uns[4] = 4, 2            # row 3 unsorted
+    out["unsorted"] = (rp, uns)
+    short = rp.copy(); short[-1] = 7                  # row_ptr[n] != nnz
+    out["row_ptr_end"] = (short, ci)
+    dec = rp.copy(); dec[3] = 2                       # decreasing offsets
+    out["row_ptr_order"] = (dec, ci)
+    return out
+
+
+@pytest.mark.parametrize("defect", sorted(_bad_structures()))
+def test_sparse_invalid_structure_is_rejected(defect):
+    rp, ci = _bad_structures()[defect]
+    vals = np.arange(1, ci.size + 1, dtype=np.float32)
+    with pytest.raises(bk.BksError) as err:
+        gpu_csr(rp, ci, vals, 6, 5)                   # checked by bks_csr_transpose
+    assert err.value.status == 1
+    a = gpu_csr(rp, ci, vals, 6, 5, transpose=False)  # checked inside the product call
+    with pytest.raises(bk.BksError) as err:
+        bk.matmul(a, dev(np.ones((5, 3), np.float32)))
+    assert err.value.status == 1
+    # the context stays usable
+    good = gpu_csr(np.array([0, 1, 2], np.int64), np.array([1, 0], np.int32),
+                   np.array([2.0, 3.0], np.float32), 2, 2)
+    y = host(bk.matmul(good, dev(np.eye(2, dtype=np.float32))))
+    assert np.array_equal(y, np.array([[0, 2], [3, 0]], np.float32))
