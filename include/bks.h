@@ -52,8 +52,10 @@ typedef enum { BKS_PREC_AUTO = 0, BKS_PREC_F64 = 1, BKS_PREC_F32 = 2, BKS_PREC_B
 
 /* The matrix A (n x d).  Paper, Sec. 1: A in R^{n x d}; the methods touch it only
  * through products with A and A^T (Sec. 4).  Dense: row-major, `vals` holds n*ld
- * elements of `dtype`.  CSR: `row_ptr` (n+1, int64), `col_idx` (nnz, int32, sorted
- * within a row), `vals` (nnz, FP32).  The optional CSR of A^T (`t_*`, d+1 / nnz /
+ * elements of `dtype`.  CSR: `row_ptr` (n+1, int64, non-decreasing from 0 to nnz),
+ * `col_idx` (nnz, int32, in [0, d) and strictly increasing within a row), `vals` (nnz,
+ * FP32); the structure is checked on the device before anything is indexed through it
+ * and a malformed CSR returns BKS_ERR_INVALID_ARG.  The optional CSR of A^T (`t_*`, d+1 / nnz /
  * nnz) lets the A^T products run row-parallel; when absent bks_csr_transpose builds
  * it.  `col_mean` (d floats, device) makes every product use A - 1 mu^T instead of A
  * (footnote 1 of Sec. 1: principal components after mean centring), applied

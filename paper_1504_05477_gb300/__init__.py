@@ -209,12 +209,15 @@ def simul_iter(a, k, q, seed=0, pi=None, want_v=False, precision="auto", stats=F
     return _solve("bks_simul_iter", a, k, q, seed, pi, want_v, precision, stats, **kw)
 
 
-def _colmajor(x):
-    """Column-major copy of a (rows x c) tensor as a (c x rows) array with row stride
-    `rows` (torch keeps stride 1 on size-1 dimensions, so .contiguous() is not enough)."""
-    out = _torch().empty((x.shape[1], x.shape[0]), dtype=x.dtype, device=x.device)
-    out.copy_(x.t())
-    return out
+def _colmajor(x, pad=1):
+    """Column-major copy of a (rows x c) tensor as a (c x ld) array, ld = rows rounded up
+    to a multiple of `pad` (torch keeps stride 1 on size-1 dimensions, so .contiguous()
+    is not enough).  Returns the (c x rows) view."""
+    rows, c = x.shape
+    ld = (rows + pad - 1) // pad * pad
+    out = _torch().zeros((c, ld), dtype=x.dtype, device=x.device)
+    out[:, :rows].copy_(x.t())
+    return out[:, :rows]
 
 
 def matmul(a, x, trans=False, simt=False, exact=False):
@@ -224,9 +227,9 @@ def matmul(a, x, trans=False, simt=False, exact=False):
     torch = _torch()
     mat, dev, _ = _as_bks(a)
     ctx = context(dev)
-    xt = _colmajor(x)
+    xt = _colmajor(x, pad=32)   # 128-byte aligned columns keep the tensor-core path open
     rows_y = mat.d if trans else mat.n
-    yt = torch.empty((x.shape[1], rows_y), dtype=x.dtype, device=x.device)
+    yt = torch.empty((x.shape[1], (rows_y + 31) // 32 * 32), dtype=x.dtype, device=x.device)[:, :rows_y]
     B.check(ctx.lib.bks_matmul(ctx.ptr, ctypes.byref(mat), int(trans), x.shape[1],
                                ctypes.c_void_p(xt.data_ptr()), xt.stride(0),
                                ctypes.c_void_p(yt.data_ptr()), yt.stride(0),

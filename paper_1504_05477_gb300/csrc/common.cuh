@@ -93,6 +93,14 @@ bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda,
                     const float* X, int64_t ldx, float* Y, int64_t ldy, float* xh, float* xl,
                     float* part, int64_t part_cap);
 int64_t tc_partial_floats(int64_t n, int64_t d, int c, int num_sms);
+// Tensor-core product with a BF16 A (kind::f16): X (FP32) is split into np = 1 (X
+// rounded to BF16) or np = 3 (FP32-accurate) BF16 pieces in xb (np * min(c, 128) * ldx
+// elements at least, xb_cap).  Returns false, launching nothing, when the operands do
+// not meet the TMA alignment rules.
+bool tc_product_bf16(Exec& ex, const __nv_bfloat16* A, int64_t n, int64_t d, int64_t lda, bool trans,
+                     int c, int np, const float* X, int64_t ldx, float* Y, int64_t ldy, __nv_bfloat16* xb,
+                     int64_t xb_cap, float* part, int64_t part_cap);
+int64_t tc_bf16_partial_floats(int64_t n, int64_t d, int c, int num_sms);
 
 // ------------------------------------------------------------------ sparse A (CSR)
 size_t csr_transpose_scratch(int64_t n, int64_t d);

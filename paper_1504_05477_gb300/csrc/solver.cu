@@ -141,6 +141,9 @@ struct ProductWs {
     float* tpart = nullptr;
     int64_t tpart_cap = 0;
     bool simt_only = false;
+    __nv_bfloat16* xb = nullptr;   // BF16 pieces of X (BF16 A)
+    int64_t xb_cap = 0;            // elements
+    int bf16_pieces = 3;           // 1: X rounded to BF16; 3: FP32-accurate
     CsrWs csr;
 };
 
@@ -227,6 +230,15 @@ void product(Exec& ex, const bks_matrix* A, bool trans, int c, const T* X, int64
         ex.product_launches += ex.launches - before;
         return;
     }
+    if (sizeof(T) == 4 && A->dtype == BKS_BF16 && !pw.simt_only && pw.xb != nullptr) {
+        const int before = ex.launches;
+        if (tc_product_bf16(ex, static_cast<const __nv_bfloat16*>(A->vals), A->n, A->d, A->ld, trans, c,
+                            pw.bf16_pieces, reinterpret_cast<const float*>(X), ldx,
+                            reinterpret_cast<float*>(Y), ldy, pw.xb, pw.xb_cap, pw.tpart, pw.tpart_cap)) {
+            ex.product_launches += ex.launches - before;
+            return;
+        }
+    }
     if (sizeof(T) == 4 && A->dtype == BKS_F32 && !pw.simt_only && pw.xh != nullptr) {
         const int before = ex.launches;
         if (tc_product_f32(ex, static_cast<const float*>(A->vals), A->n, A->d, A->ld, trans, c,
@@ -255,8 +267,8 @@ void product(Exec& ex, const bks_matrix* A, bool trans, int c, const T* X, int64
 struct Plan {
     int64_t n, d, ldn, ldd;
     int k, q, w;
-    size_t xh, xl, tpart;
-    int64_t tpart_cap;
+    size_t xh, xl, tpart, xb;
+    int64_t tpart_cap, xb_cap;
     bool sparse;
     CsrLayout csr;
     size_t Qt, Bt, QBt, Pit, W, Wtmp, Wb, Wbtmp, part, gram, rfac, ct, Rm, JX, lam, nrm, Vt,
@@ -315,7 +327,16 @@ Plan make_plan(const bks_matrix* A, int k, int q_eff, int w, size_t tb, int sms)
     p.xh = a.take(size_t(k) * ldmax * 4);
     p.xl = a.take(size_t(k) * ldmax * 4);
     p.tpart_cap = tc_partial_floats(n, d, k, sms);
+    p.xb_cap = 0;
+    if (A->kind == BKS_DENSE && A->dtype == BKS_BF16) {
+        // the refinement product runs at width w in groups of up to 128 columns
+        const int cmax = w > k ? (w < 128 ? w : 128) : k;
+        const int64_t b = tc_bf16_partial_floats(n, d, cmax, sms);
+        if (b > p.tpart_cap) p.tpart_cap = b;
+        p.xb_cap = 3 * int64_t(cmax) * ldmax;
+    }
     p.tpart = a.take(size_t(p.tpart_cap) * 4);
+    p.xb = a.take(size_t(p.xb_cap) * 2 + 16);
     p.stat = a.take(4 * sizeof(int));
     p.sparse = A->kind == BKS_CSR;
     if (p.sparse) p.csr.take(a, A, k);
@@ -409,6 +430,13 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
     pw.tpart = reinterpret_cast<float*>(base + p.tpart);
     pw.tpart_cap = p.tpart_cap;
     pw.simt_only = o.product_path == 1;
+    pw.xb = p.xb_cap > 0 ? reinterpret_cast<__nv_bfloat16*>(base + p.xb) : nullptr;
+    pw.xb_cap = p.xb_cap;
+    // Mixed precision (BF16 A): the Krylov products take X rounded to BF16; with refine,
+    // B = A^T Q is recomputed FP32-accurately at the full width before Rayleigh-Ritz.
+    const bool bf16_mode = o.precision == BKS_PREC_BF16;
+    const bool refine = bf16_mode && o.refine != 0;
+    pw.bf16_pieces = bf16_mode ? 1 : 3;
     int* stat = reinterpret_cast<int*>(base + p.stat);   // [status, sweeps, shifted]
     T* Z = static_cast<T*>(Zv);
     T* sigma = static_cast<T*>(sigv);
@@ -433,9 +461,9 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
     else
         gen_pi_device<T>(ex, seed, d, k, Pit, p.ldd, true);
 
-    auto prod = [&](bool trans, const T* X, int64_t ldx, T* Y, int64_t ldy) {
+    auto prod = [&](bool trans, const T* X, int64_t ldx, T* Y, int64_t ldy, int c) {
         const int b = prof.begin();
-        product<T>(ex, A, trans, k, X, ldx, Y, ldy, part, p.part_cap, pw);
+        product<T>(ex, A, trans, c, X, ldx, Y, ldy, part, p.part_cap, pw);
         prof.end(0, b);
     };
     auto orth = [&](int m, T* Qout) {
@@ -455,14 +483,14 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
     };
 
     // a1 + a4: W_0 = A Pi, Q_0 = orth(W_0)
-    prod(false, Pit, p.ldd, W, p.ldn);
+    prod(false, Pit, p.ldd, W, p.ldn, k);
     orth(0, Qt);
     for (int i = 1; i <= q_eff; ++i) {
         T* Qprev = krylov ? Qt + size_t(i - 1) * k * p.ldn : Qt;
         T* Bprev = krylov ? Bt + size_t(i - 1) * k * p.ldd : Bt;
-        prod(true, Qprev, p.ldn, Bprev, p.ldd);          // a2: B_{i-1} = A^T Q_{i-1}
-        if (krylov && !o.basis_only) orth_b((i - 1) * k, Bprev);
-        prod(false, Bprev, p.ldd, W, p.ldn);              // a3: W_i = A B_{i-1}
+        prod(true, Qprev, p.ldn, Bprev, p.ldd, k);       // a2: B_{i-1} = A^T Q_{i-1}
+        if (krylov && !o.basis_only && !refine) orth_b((i - 1) * k, Bprev);
+        prod(false, Bprev, p.ldd, W, p.ldn, k);           // a3: W_i = A B_{i-1}
         if (krylov)
             orth(i * k, Qt + size_t(i) * k * p.ldn);     // a4: project + CholeskyQR2
         else
@@ -470,7 +498,15 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
     }
     T* Blast = krylov ? Bt + size_t(q_eff) * k * p.ldd : Bt;
     const T* Qlast = krylov ? Qt + size_t(q_eff) * k * p.ldn : Qt;
-    prod(true, Qlast, p.ldn, Blast, p.ldd);               // a5: B_q = A^T Q_q
+    if (!refine) {
+        prod(true, Qlast, p.ldn, Blast, p.ldd, k);        // a5: B_q = A^T Q_q
+    } else {
+        // a8: B = A^T Q at the full width, FP32-accurate (three BF16 pieces of Q)
+        pw.bf16_pieces = 3;
+        prod(true, Qt, p.ldn, Bt, p.ldd, w);
+        if (krylov && !o.basis_only)
+            for (int i = 0; i < q_eff; ++i) orth_b(i * k, Bt + size_t(i) * k * p.ldd);
+    }
 
     const int t_rr = prof.begin();
     if (o.basis_only) {
@@ -540,9 +576,14 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
         const double abytes = A->kind == BKS_CSR
                                   ? double(A->nnz) * 8.0 + double(n + d + 2) * 4.0
                                   : double(n) * double(A->ld) * double(dtype_bytes(A->dtype));
+        const double nnz_like = A->kind == BKS_CSR ? double(A->nnz) : double(n) * double(d);
         st->product_bytes = nprod * (abytes + double(k) * (n + d) * sizeof(T));
-        st->product_flops = nprod * 2.0 * k *
-                            (A->kind == BKS_CSR ? double(A->nnz) : double(n) * double(d));
+        st->product_flops = nprod * 2.0 * k * nnz_like;
+        if (refine) {   // the last A^T product runs at width w (groups of 128 columns)
+            const double groups = double((w + 127) / 128);
+            st->product_bytes += groups * abytes + double(w - k) * (n + d) * sizeof(T);
+            st->product_flops += 2.0 * (w - k) * nnz_like;
+        }
         if (o.profile) {
             st->ms_product = prof.total(0);
             st->ms_orth = prof.total(1);
@@ -584,12 +625,16 @@ bks_status solve_entry(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t
     if (opts) o = *opts; else bks_opts_default(&o);
     int prec = o.precision;
     if (prec == BKS_PREC_AUTO) prec = A->dtype == BKS_F64 ? BKS_PREC_F64 : BKS_PREC_F32;
-    if (prec == BKS_PREC_BF16) return fail(ctx, BKS_ERR_UNSUPPORTED, "BF16 precision mode is not built yet");
-    if (prec != BKS_PREC_F64 && prec != BKS_PREC_F32) return fail(ctx, BKS_ERR_INVALID_ARG, "bad precision");
+    if (prec != BKS_PREC_F64 && prec != BKS_PREC_F32 && prec != BKS_PREC_BF16)
+        return fail(ctx, BKS_ERR_INVALID_ARG, "bad precision");
+    if (prec == BKS_PREC_BF16 && (A->kind != BKS_DENSE || A->dtype != BKS_BF16))
+        return fail(ctx, BKS_ERR_UNSUPPORTED, "the BF16 mode needs a dense BF16 A");
+    o.precision = prec;
     DeviceGuard g(ctx->device);
     if (A->kind == BKS_CSR && prec != BKS_PREC_F32)
         return fail(ctx, BKS_ERR_UNSUPPORTED, "a CSR matrix is solved on the FP32 path");
     if (prec == BKS_PREC_F64) return solve<double>(ctx, A, k, q, seed, pi, Z, sigma, V, o, st, krylov);
+    // BF16 and F32 both run the FP32 pipeline (Krylov blocks, Z, sigma in FP32)
     return solve<float>(ctx, A, k, q, seed, pi, Z, sigma, V, o, st, krylov);
 }
 
@@ -781,11 +826,18 @@ bks_status bks_matmul(bks_ctx* ctx, const bks_matrix* A, int trans, int c, const
     DeviceGuard g(ctx->device);
     const bool f64 = A->dtype == BKS_F64;
     const int64_t cap = gemm_partial_elems(c, rows_y, rows_x, ctx->num_sms);
-    const int64_t tcap = tc_partial_floats(A->n, A->d, c < 128 ? c : 128, ctx->num_sms);
+    int64_t tcap = tc_partial_floats(A->n, A->d, c < 128 ? c : 128, ctx->num_sms);
+    const bool bf16_a = A->kind == BKS_DENSE && A->dtype == BKS_BF16;
+    const int64_t xb_cap = bf16_a ? 3 * int64_t(c < 128 ? c : 128) * ldx : 0;
+    if (bf16_a) {
+        const int64_t b = tc_bf16_partial_floats(A->n, A->d, c < 128 ? c : 128, ctx->num_sms);
+        if (b > tcap) tcap = b;
+    }
     Arena ar;
     const size_t o_part = ar.take(size_t(cap) * sizeof(double) + 8),
                  o_xh = ar.take(size_t(c) * ldx * 4), o_xl = ar.take(size_t(c) * ldx * 4),
-                 o_tp = ar.take(size_t(tcap) * 4), o_stat = ar.take(16);
+                 o_tp = ar.take(size_t(tcap) * 4), o_stat = ar.take(16),
+                 o_xb = ar.take(size_t(xb_cap) * 2 + 16);
     CsrLayout cl{};
     if (A->kind == BKS_CSR) cl.take(ar, A, c);
     s = ensure_ws(ctx, ar.off);
@@ -801,6 +853,11 @@ bks_status bks_matmul(bks_ctx* ctx, const bks_matrix* A, int trans, int c, const
     pw.tpart = reinterpret_cast<float*>(wsb + o_tp);
     pw.tpart_cap = tcap;
     pw.simt_only = (flags & BKS_MATMUL_SIMT) != 0;
+    if (bf16_a) {
+        pw.xb = reinterpret_cast<__nv_bfloat16*>(wsb + o_xb);
+        pw.xb_cap = xb_cap;
+        pw.bf16_pieces = (flags & BKS_MATMUL_EXACT) ? 3 : 1;
+    }
     int* stat = reinterpret_cast<int*>(wsb + o_stat);
     ex.status = stat;
     cudaMemsetAsync(stat, 0, 16, ctx->stream);

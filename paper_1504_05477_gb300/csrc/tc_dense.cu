@@ -20,102 +20,19 @@
 //   warps 7-10  epilogue: tcgen05.ld the accumulator, add the halves, store
 // Every wait is bounded (1 s of globaltimer); on timeout the CTA records
 // ST_TIMEOUT, drains what it issued (bounded again), frees its TMEM and returns.
-#include <cuda.h>
-#include <cudaTypedefs.h>
-
-#include "common.cuh"
+#include "tc_common.cuh"
 
 namespace bks {
 namespace tc {
 
-constexpr int BM = 128;            // UMMA M: rows of D per tile
 constexpr int KC = 32;             // contraction depth per chunk (128 bytes of FP32)
 constexpr int RA = 6;              // raw A ring depth
 constexpr int OP = 2;              // operand ring depth
 constexpr int NWARP = 11;
 constexpr int NTHREADS = NWARP * 32;
 constexpr uint32_t TILE_BYTES = BM * KC * 4;   // 16 KB
-constexpr uint64_t WAIT_NS = 1000000000ull;    // 1 s
 constexpr int FLUSH = 4;           // chunks (32 tf32 MMA steps) per TMEM accumulation window
 
-struct Params {
-    int mode;          // 0: AX, 1: ATX
-    int c;             // real output columns (<= 128)
-    int cp;            // padded columns (32, 64, 96, 128)
-    int64_t rows_out;  // extent of the tiled dimension (n for AX, d for ATX)
-    int64_t tiles;     // ceil(rows_out / BM)
-    int64_t cpt;       // chunks per tile (contraction length / KC, rounded up)
-    float* out;        // c x ldo
-    int64_t ldo;
-    float* part;       // partial tiles: [grid][maxseg][cp][BM]
-    int maxseg;
-    int* status;
-};
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(
-                     smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ uint64_t gtimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// Bounded wait: false on timeout (status flagged, abort raised) or when another role
-// already aborted.
-__device__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
-    if (mbar_try(bar, parity)) return true;
-    const uint64_t t0 = gtimer();
-    while (true) {
-        if (mbar_try(bar, parity)) return true;
-        if (*abort_flag) return false;
-        if (gtimer() - t0 > WAIT_NS) {
-            atomicOr(status, ST_TIMEOUT);
-            *abort_flag = 1;
-            return false;
-        }
-    }
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
-        "{%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-// UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, 8-row atoms 1024 B apart.
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
-    uint64_t d = uint64_t((saddr & 0x3FFFF) >> 4);
-    d |= uint64_t(16 >> 4) << 16;      // leading byte offset (unused for swizzled K-major)
-    d |= uint64_t(1024 >> 4) << 32;    // stride byte offset
-    d |= uint64_t(1) << 46;            // descriptor version
-    d |= uint64_t(2) << 61;            // 128-byte swizzle
-    return d;
-}
 // Instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major, M = 128.
 __host__ __device__ constexpr uint32_t idesc_tf32(int n) {
     return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(BM >> 4) << 24);
@@ -127,38 +44,6 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
-        "%28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ float tf32_hi(float v) {
     return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
@@ -172,18 +57,6 @@ struct Smem {
     uint32_t tmem_base;
     int abort_flag;
 };
-
-// Units of CTA `cta`: [start, end) in the flattened (tile, chunk) order.
-__device__ __forceinline__ void unit_range(int64_t U, int G, int cta, int64_t& s, int64_t& e) {
-    s = (int64_t(cta) * U) / G;
-    e = (int64_t(cta + 1) * U) / G;
-}
-
-// A new accumulation window starts at the CTA's first unit, at every tile boundary and
-// every FLUSH chunks within a tile.
-__device__ __forceinline__ bool window_start(int64_t u, int64_t ustart, int64_t cpt) {
-    return u == ustart || (u % cpt) % FLUSH == 0;
-}
 
 template <int CP>
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -249,12 +122,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 last[s] = int((i / RA) & 1);
             }
             // every load issued has landed before shared memory is released (bounded)
-            for (int s = 0; s < RA; ++s) {
-                if (last[s] < 0) continue;
-                const uint64_t t0 = gtimer();
-                while (!mbar_try(&sm->raw_full[s], uint32_t(last[s])) && gtimer() - t0 < WAIT_NS) {
-                }
-            }
+            for (int s = 0; s < RA; ++s) drain_bar(&sm->raw_full[s], last[s]);
         }
     } else if (warp == 1) {
         // ---------------------------------------------------------------- X producer
@@ -272,12 +140,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tma_load_2d(dst + CP * 128, &tmXl, int(kc * KC), 0, &sm->b_full[o]);
                 last[o] = int((i / OP) & 1);
             }
-            for (int o = 0; o < OP; ++o) {
-                if (last[o] < 0) continue;
-                const uint64_t t0 = gtimer();
-                while (!mbar_try(&sm->b_full[o], uint32_t(last[o])) && gtimer() - t0 < WAIT_NS) {
-                }
-            }
+            for (int o = 0; o < OP; ++o) drain_bar(&sm->b_full[o], last[o]);
         }
     } else if (warp == 2) {
         // ---------------------------------------------------------------- MMA issuer
@@ -288,7 +151,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             bool first = true;
             for (int64_t u = ustart; u < uend; ++u, ++i) {
                 const int64_t t = u / p.cpt;
-                if (window_start(u, ustart, p.cpt)) {
+                if (window_start(u, ustart, p.cpt, FLUSH)) {
                     ++sub;
                     if (!wait_bar(&sm->acc_empty[sub & 1], uint32_t(((sub >> 1) & 1) ^ 1), abort_flag, p.status)) break;
                     tc_fence_after();
@@ -312,7 +175,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 first = false;
                 umma_commit(&sm->op_empty[o]);
-                if (u + 1 == uend || window_start(u + 1, ustart, p.cpt))
+                if (u + 1 == uend || window_start(u + 1, ustart, p.cpt, FLUSH))
                     umma_commit(&sm->acc_full[sub & 1]);
             }
             // drain: every MMA issued so far has completed before TMEM is released
@@ -389,7 +252,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             for (int j = 0; j < CP; ++j) run[j] = 0.f;
             while (u < seg_end) {
                 int64_t w_end = u + 1;
-                while (w_end < seg_end && !window_start(w_end, ustart, p.cpt)) ++w_end;
+                while (w_end < seg_end && !window_start(w_end, ustart, p.cpt, FLUSH)) ++w_end;
                 ++sub;
                 if (!wait_bar(&sm->acc_full[sub & 1], uint32_t((sub >> 1) & 1), abort_flag, p.status)) {
                     ok = false;
@@ -498,8 +361,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-bool encode_2d(CUtensorMap* map, const void* ptr, uint64_t inner, uint64_t outer,
-               uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle sw) {
+bool encode_2d(CUtensorMap* map, CUtensorMapDataType type, const void* ptr, uint64_t inner,
+               uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer,
+               CUtensorMapSwizzle sw) {
     auto fn = encode_fn();
     if (fn == nullptr) return false;
     if ((reinterpret_cast<uintptr_t>(ptr) & 15) != 0 || (row_bytes & 15) != 0) return false;
@@ -507,9 +371,20 @@ bool encode_2d(CUtensorMap* map, const void* ptr, uint64_t inner, uint64_t outer
     cuuint64_t strides[1] = {row_bytes};
     cuuint32_t box[2] = {box_inner, box_outer};
     cuuint32_t estr[2] = {1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box,
+    return fn(map, type, 2, const_cast<void*>(ptr), dims, strides, box,
               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+void fixup(Exec& ex, const Params& p, int G) {
+    tc_fixup_kernel<<<dim3(unsigned(p.tiles), unsigned((p.c + 7) / 8)), 2 * BM, 0, ex.stream>>>(p, G);
+    ex.launches++;
+}
+
+int64_t partial_floats(int64_t rows_out, int64_t len, int kc, int cp, int num_sms) {
+    const int64_t tiles = (rows_out + BM - 1) / BM, cpt = (len + kc - 1) / kc;
+    const int64_t U = tiles * cpt, G = U < num_sms ? U : num_sms, per = (U + G - 1) / G;
+    return G * (per / cpt + 2) * cp * BM;
 }
 
 size_t smem_bytes(int cp) {
@@ -534,10 +409,10 @@ bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda,
     if (len > INT32_MAX || rows_out > INT32_MAX) return false;
     CUtensorMap tmA;
     if (!trans) {
-        if (!encode_2d(&tmA, A, uint64_t(d), uint64_t(n), uint64_t(lda) * 4, KC, BM, CU_TENSOR_MAP_SWIZZLE_128B))
+        if (!encode_2d(&tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, uint64_t(d), uint64_t(n), uint64_t(lda) * 4, KC, BM, CU_TENSOR_MAP_SWIZZLE_128B))
             return false;
     } else {
-        if (!encode_2d(&tmA, A, uint64_t(d), uint64_t(n), uint64_t(lda) * 4, BM, KC, CU_TENSOR_MAP_SWIZZLE_NONE))
+        if (!encode_2d(&tmA, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, A, uint64_t(d), uint64_t(n), uint64_t(lda) * 4, BM, KC, CU_TENSOR_MAP_SWIZZLE_NONE))
             return false;
     }
     const int G = ex.num_sms;
@@ -555,9 +430,9 @@ bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda,
             ex.launches++;
         }
         CUtensorMap tmXh, tmXl;
-        if (!encode_2d(&tmXh, xhg, uint64_t(len), uint64_t(cg), uint64_t(ldx) * 4, KC, uint32_t(cp),
+        if (!encode_2d(&tmXh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, xhg, uint64_t(len), uint64_t(cg), uint64_t(ldx) * 4, KC, uint32_t(cp),
                        CU_TENSOR_MAP_SWIZZLE_128B) ||
-            !encode_2d(&tmXl, xlg, uint64_t(len), uint64_t(cg), uint64_t(ldx) * 4, KC, uint32_t(cp),
+            !encode_2d(&tmXl, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, xlg, uint64_t(len), uint64_t(cg), uint64_t(ldx) * 4, KC, uint32_t(cp),
                        CU_TENSOR_MAP_SWIZZLE_128B))
             return false;
         Params p{};
@@ -597,23 +472,17 @@ bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda,
             cudaGetLastError();
             return false;
         }
-        tc_fixup_kernel<<<dim3(unsigned(p.tiles), unsigned((cg + 7) / 8)), 2 * BM, 0, ex.stream>>>(p, Gc);
-        ex.launches += 2;
+        fixup(ex, p, Gc);
+        ex.launches++;
     }
     return true;
 }
 
 int64_t tc_partial_floats(int64_t n, int64_t d, int c, int num_sms) {
-    int64_t best = 0;
-    for (int trans = 0; trans < 2; ++trans) {
-        const int64_t len = trans ? n : d, rows_out = trans ? d : n;
-        const int cp = ((c < 128 ? c : 128) + 31) / 32 * 32;
-        const int64_t tiles = (rows_out + tc::BM - 1) / tc::BM, cpt = (len + tc::KC - 1) / tc::KC;
-        const int64_t U = tiles * cpt, per = (U + num_sms - 1) / num_sms;
-        const int64_t need = int64_t(num_sms) * (per / cpt + 2) * cp * tc::BM;
-        if (need > best) best = need;
-    }
-    return best;
+    const int cp = ((c < 128 ? c : 128) + 31) / 32 * 32;
+    const int64_t a = tc::partial_floats(n, d, tc::KC, cp, num_sms);   // A X
+    const int64_t b = tc::partial_floats(d, n, tc::KC, cp, num_sms);   // A^T X
+    return a > b ? a : b;
 }
 
 }  // namespace bks

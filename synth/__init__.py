@@ -175,6 +175,40 @@ def dense_bf16_planted(m=65536, d=16384, seed=1004, rows=None, chunk=1024):
     return bf16_round(out), sigma
 
 
+def dense_bf16_planted_torch(m=65536, d=16384, seed=1004, rows=None, device="cuda", chunk=4096):
+    """dense_bf16_planted computed with torch on `device` (a GPU builds the 65536 x 16384
+    matrix in seconds): the same FP64 operations in the same order, so the result is
+    bitwise identical.  Returns a torch.bfloat16 tensor (rows x d) on `device`."""
+    import torch
+    rng = np.random.default_rng(seed)
+    d1 = rng.choice([-1.0, 1.0], size=m)[:d]
+    d2 = rng.choice([-1.0, 1.0], size=d)
+    sigma = np.arange(1, d + 1, dtype=np.float64) ** -0.5
+    scale = torch.from_numpy(d2 * sigma * d1 / np.sqrt(float(m) * float(d))).to(device)
+    rows = np.arange(m) if rows is None else np.asarray(rows)
+    cidx = torch.arange(d, dtype=torch.int64, device=device)
+    out = torch.empty((rows.size, d), dtype=torch.bfloat16, device=device)
+    for i0 in range(0, rows.size, chunk):
+        r = torch.from_numpy(rows[i0:i0 + chunk].astype(np.int64)).to(device)
+        pc = torch.bitwise_and(r[:, None], cidx[None, :])
+        par = torch.zeros_like(pc)
+        while bool(torch.any(pc)):
+            par ^= pc & 1
+            pc >>= 1
+        y = (1.0 - 2.0 * par.to(torch.float64)) * scale
+        h = 1
+        while h < d:   # the butterflies of _fwht_rows, same order
+            y = y.reshape(y.shape[0], d // (2 * h), 2, h)
+            a = y[:, :, 0, :].clone()
+            b = y[:, :, 1, :]
+            y[:, :, 0, :] = a + b
+            y[:, :, 1, :] = a - b
+            y = y.reshape(y.shape[0], d)
+            h *= 2
+        out[i0:i0 + chunk] = y.to(torch.float32).to(torch.bfloat16)
+    return out
+
+
 def batched_planted(batch=256, k=16, seed=1005, m_range=(256, 4096), n_range=(128, 2048),
                     noise=1e-3):
     """List of dense FP32 matrices with m ~ U[256, 4096], n ~ U[128, 2048] integer shapes,
