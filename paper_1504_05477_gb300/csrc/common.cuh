@@ -89,9 +89,10 @@ int64_t gemm_partial_elems(int64_t M, int64_t N, int64_t K, int num_sms);
 // or (A^T X)^T (trans true), thin blocks column-major.  xh/xl: c x ldx scratch each;
 // part: tc_partial_floats(...) floats.  Returns false, launching nothing, when the
 // operands do not meet the TMA alignment rules.
+// subtract: Y -= the product (Y is read) instead of Y = the product.
 bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda, bool trans, int c,
                     const float* X, int64_t ldx, float* Y, int64_t ldy, float* xh, float* xl,
-                    float* part, int64_t part_cap);
+                    float* part, int64_t part_cap, bool subtract = false);
 int64_t tc_partial_floats(int64_t n, int64_t d, int c, int num_sms);
 // Tensor-core product with a BF16 A (kind::f16): X (FP32) is split into np = 1 (X
 // rounded to BF16) or np = 3 (FP32-accurate) BF16 pieces in xb (np * min(c, 128) * ldx
@@ -135,15 +136,35 @@ template <typename T>
 void transpose_in(Exec& ex, const void* src, int src_dtype, int64_t rows, int64_t cols,
                   int64_t lds, T* dst, int64_t ldd);
 
-// Block orthonormalisation: W (c x ld thin) against Qb (m x ld thin), result in Qout.
-// ct: c x m scratch; gram: max(m, c) x c FP64; rfac: c x c; shifted_flag: device int.
+// Scratch of the block orthonormalisation (pointers into the caller's workspace).
+struct OrthWs {
+    double* partials = nullptr;   // SIMT split-K partials (cap doubles)
+    int64_t cap = 0;
+    void* g = nullptr;            // c x ldp Gram matrix (T)
+    void* rfac = nullptr;         // c x ldp, P = R^{-T} (T)
+    int ldp = 0;
+    void* ct = nullptr;           // c x ldc projection coefficients (T)
+    int64_t ldc = 0;
+    float* xh = nullptr;          // tensor-core path (FP32 only; nullptr disables it):
+    float* xl = nullptr;          //   c x ld_max hi / lo split of the X operand
+    float* tpart = nullptr;       //   stream-K partial tiles
+    int64_t tpart_cap = 0;
+    int* shifted_flag = nullptr;  // device int: a Cholesky needed a diagonal shift
+};
+// Byte sizes of those buffers for blocks of c columns, at most mmax earlier columns and
+// lengths up to len_max (pitch up to ld_max).
+struct OrthSizes {
+    size_t partials, g, rfac, ct, xh, tpart;
+    int ldp;
+    int64_t ldc, cap, tcap;
+};
+OrthSizes orth_sizes(int64_t len_max, int64_t ld_max, int mmax, int c, int elem_bytes, bool tc, int num_sms);
+
+// Block orthonormalisation: W (c x ld thin) against Qb (m x ld thin), BCGS2 then
+// CholeskyQR2, result in Qout (may equal W); Wtmp: c x ld scratch.
 template <typename T>
-void orth_block(Exec& ex, int64_t len, int64_t ld, const T* Qb, int m, T* W, int c, T* Wtmp,
-                T* Qout, double* partials, int64_t partial_cap, double* gram, T* rfac, T* ct,
-                int* shifted_flag);
-template <typename T>
-void cholqr_extra(Exec& ex, int64_t len, int64_t ld, T* Q, int c, double* partials, int64_t cap,
-                  double* gram, T* rfac, int* shifted_flag, T* tmp);
+void orth_block(Exec& ex, int64_t len, int64_t ld, const T* Qb, int m, T* W, int c, T* Wtmp, T* Qout,
+                const OrthWs& ws);
 // Jacobi launch plan (cluster size C, block width b, register tile E, shared bytes).
 bool jacobi_plan(int w, int elem_bytes, int& C, int& b, int& E, size_t& smem);
 

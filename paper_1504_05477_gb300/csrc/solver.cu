@@ -271,8 +271,10 @@ struct Plan {
     int64_t tpart_cap, xb_cap;
     bool sparse;
     CsrLayout csr;
-    size_t Qt, Bt, QBt, Pit, W, Wtmp, Wb, Wbtmp, part, gram, rfac, ct, Rm, JX, lam, nrm, Vt,
+    size_t Qt, Bt, QBt, Pit, W, Wtmp, Wb, Wbtmp, part, og, rfac, ct, Rm, JX, lam, nrm, Vt,
         order, Vk, stat;
+    int ldp;
+    int64_t ldc;
     int64_t part_cap;
     size_t total;
 };
@@ -285,14 +287,9 @@ int64_t max_partials(int64_t n, int64_t d, int k, int w, int sms) {
     };
     upd(k, n, d);        // A X
     upd(k, d, n);        // A^T X
-    upd(w, k, n);        // projection coefficients
-    upd(k, n, w);        // projection update, Z = Q Ubar_k
-    upd(k, k, n);        // Gram
-    upd(w, k, d);        // d-space projection coefficients (QR of B)
-    upd(k, d, w);        // d-space projection update, B Ubar_k
-    upd(k, k, d);        // d-space Gram
+    upd(k, n, w);        // Z = Q Ubar_k
+    upd(k, d, w);        // B Ubar_k
     upd(w, w, d);        // R = Q_B^T B
-    if (p < int64_t(k) * k) p = int64_t(k) * k;   // FP64 Gram output always uses partials
     return p;
 }
 
@@ -311,11 +308,18 @@ Plan make_plan(const bks_matrix* A, int k, int q_eff, int w, size_t tb, int sms)
     p.Wtmp = a.take(size_t(k) * p.ldn * tb);
     p.Wb = a.take(size_t(k) * p.ldd * tb);
     p.Wbtmp = a.take(size_t(k) * p.ldd * tb);
+    const int64_t ldmax0 = p.ldn > p.ldd ? p.ldn : p.ldd;
+    const OrthSizes on = orth_sizes(n, p.ldn, w, k, int(tb), tb == 4, sms);
+    const OrthSizes od = orth_sizes(d, p.ldd, w, k, int(tb), tb == 4, sms);
     p.part_cap = max_partials(n, d, k, w, sms);
+    if (on.cap > p.part_cap) p.part_cap = on.cap;
+    if (od.cap > p.part_cap) p.part_cap = od.cap;
     p.part = a.take(size_t(p.part_cap) * sizeof(double));
-    p.gram = a.take(size_t(w) * k * sizeof(double));
-    p.rfac = a.take(size_t(k) * k * tb);
-    p.ct = a.take(size_t(k) * w * tb);
+    p.ldp = on.ldp;
+    p.ldc = on.ldc;
+    p.og = a.take(on.g);
+    p.rfac = a.take(on.rfac);
+    p.ct = a.take(on.ct);
     p.Rm = a.take(size_t(w) * w * tb);
     p.JX = a.take(size_t(w) * w * tb);
     p.lam = a.take(size_t(w) * tb);
@@ -327,6 +331,9 @@ Plan make_plan(const bks_matrix* A, int k, int q_eff, int w, size_t tb, int sms)
     p.xh = a.take(size_t(k) * ldmax * 4);
     p.xl = a.take(size_t(k) * ldmax * 4);
     p.tpart_cap = tc_partial_floats(n, d, k, sms);
+    if (on.tcap > p.tpart_cap) p.tpart_cap = on.tcap;
+    if (od.tcap > p.tpart_cap) p.tpart_cap = od.tcap;
+    (void)ldmax0;
     p.xb_cap = 0;
     if (A->kind == BKS_DENSE && A->dtype == BKS_BF16) {
         // the refinement product runs at width w in groups of up to 128 columns
@@ -414,9 +421,14 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
     T* Wb = reinterpret_cast<T*>(base + p.Wb);
     T* Wbtmp = reinterpret_cast<T*>(base + p.Wbtmp);
     double* part = reinterpret_cast<double*>(base + p.part);
-    double* gram = reinterpret_cast<double*>(base + p.gram);
-    T* rfac = reinterpret_cast<T*>(base + p.rfac);
-    T* ct = reinterpret_cast<T*>(base + p.ct);
+    OrthWs ows;
+    ows.partials = part;
+    ows.cap = p.part_cap;
+    ows.g = base + p.og;
+    ows.rfac = base + p.rfac;
+    ows.ldp = p.ldp;
+    ows.ct = base + p.ct;
+    ows.ldc = p.ldc;
     T* Rm = reinterpret_cast<T*>(base + p.Rm);
     T* JX = reinterpret_cast<T*>(base + p.JX);
     T* lam = reinterpret_cast<T*>(base + p.lam);
@@ -466,10 +478,16 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
         product<T>(ex, A, trans, c, X, ldx, Y, ldy, part, p.part_cap, pw);
         prof.end(0, b);
     };
+    ows.shifted_flag = stat + 2;
+    if (sizeof(T) == 4 && o.product_path != 1) {   // thin-block products on the tensor cores
+        ows.xh = pw.xh;
+        ows.xl = pw.xl;
+        ows.tpart = pw.tpart;
+        ows.tpart_cap = pw.tpart_cap;
+    }
     auto orth = [&](int m, T* Qout) {
         const int b = prof.begin();
-        orth_block<T>(ex, n, p.ldn, Qt, m, W, k, Wtmp, Qout, part, p.part_cap, gram, rfac, ct,
-                      stat + 2);
+        orth_block<T>(ex, n, p.ldn, Qt, m, W, k, Wtmp, Qout, ows);
         prof.end(1, b);
     };
     // QR of the kept blocks B_i in d-space (R = Q_B^T B preconditions the eigen-solve)
@@ -477,8 +495,7 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
         const int b = prof.begin();
         cudaMemcpyAsync(Wb, Bblk, size_t(k) * p.ldd * sizeof(T), cudaMemcpyDeviceToDevice,
                         ctx->stream);
-        orth_block<T>(ex, d, p.ldd, QBt, m, Wb, k, Wbtmp, QBt + size_t(m) * p.ldd, part,
-                      p.part_cap, gram, rfac, ct, stat + 2);
+        orth_block<T>(ex, d, p.ldd, QBt, m, Wb, k, Wbtmp, QBt + size_t(m) * p.ldd, ows);
         prof.end(1, b);
     };
 
@@ -887,15 +904,11 @@ bks_status bks_orthonormalize(bks_ctx* ctx, int dtype, int64_t len, int m, int c
         return fail(ctx, BKS_ERR_INVALID_ARG, "bad bks_orthonormalize arguments (ldq must equal ldw)");
     DeviceGuard g(ctx->device);
     const size_t tb = dtype == BKS_F64 ? 8 : 4;
-    const int mm = m > 0 ? m : 1;
-    int64_t cap = 0;
-    for (int64_t e : {gemm_partial_elems(mm, c, len, ctx->num_sms),
-                      gemm_partial_elems(c, len, mm, ctx->num_sms),
-                      gemm_partial_elems(c, c, len, ctx->num_sms), int64_t(c) * c})
-        if (e > cap) cap = e;
+    const bool tc = dtype == BKS_F32;
+    const OrthSizes z = orth_sizes(len, ldw, m, c, int(tb), tc, ctx->num_sms);
     Arena a;
-    const size_t o_part = a.take(size_t(cap) * 8), o_gram = a.take(size_t(c) * c * 8),
-                 o_rfac = a.take(size_t(c) * c * tb), o_ct = a.take(size_t(c) * mm * tb),
+    const size_t o_part = a.take(z.partials), o_g = a.take(z.g), o_rfac = a.take(z.rfac),
+                 o_ct = a.take(z.ct), o_xh = a.take(z.xh), o_xl = a.take(z.xh), o_tp = a.take(z.tpart),
                  o_wtmp = a.take(size_t(c) * ldw * tb), o_stat = a.take(16);
     bks_status s = ensure_ws(ctx, a.off);
     if (s != BKS_OK) return s;
@@ -906,20 +919,27 @@ bks_status bks_orthonormalize(bks_ctx* ctx, int dtype, int64_t len, int m, int c
     int* stat = reinterpret_cast<int*>(base + o_stat);
     ex.status = stat;
     cudaMemsetAsync(stat, 0, 16, ctx->stream);
+    OrthWs ws;
+    ws.partials = reinterpret_cast<double*>(base + o_part);
+    ws.cap = z.cap;
+    ws.g = base + o_g;
+    ws.rfac = base + o_rfac;
+    ws.ldp = z.ldp;
+    ws.ct = base + o_ct;
+    ws.ldc = z.ldc;
+    ws.shifted_flag = stat + 2;
+    if (tc) {
+        ws.xh = reinterpret_cast<float*>(base + o_xh);
+        ws.xl = reinterpret_cast<float*>(base + o_xl);
+        ws.tpart = reinterpret_cast<float*>(base + o_tp);
+        ws.tpart_cap = z.tcap;
+    }
     if (dtype == BKS_F64)
-        orth_block<double>(ex, len, ldw, static_cast<const double*>(Qb), m, static_cast<double*>(W),
-                           c, reinterpret_cast<double*>(base + o_wtmp), static_cast<double*>(W),
-                           reinterpret_cast<double*>(base + o_part), cap,
-                           reinterpret_cast<double*>(base + o_gram),
-                           reinterpret_cast<double*>(base + o_rfac),
-                           reinterpret_cast<double*>(base + o_ct), stat + 2);
+        orth_block<double>(ex, len, ldw, static_cast<const double*>(Qb), m, static_cast<double*>(W), c,
+                           reinterpret_cast<double*>(base + o_wtmp), static_cast<double*>(W), ws);
     else
         orth_block<float>(ex, len, ldw, static_cast<const float*>(Qb), m, static_cast<float*>(W), c,
-                          reinterpret_cast<float*>(base + o_wtmp), static_cast<float*>(W),
-                          reinterpret_cast<double*>(base + o_part), cap,
-                          reinterpret_cast<double*>(base + o_gram),
-                          reinterpret_cast<float*>(base + o_rfac),
-                          reinterpret_cast<float*>(base + o_ct), stat + 2);
+                          reinterpret_cast<float*>(base + o_wtmp), static_cast<float*>(W), ws);
     cudaError_t e = cudaMemcpyAsync(ctx->host_status, stat, 3 * sizeof(int), cudaMemcpyDeviceToHost,
                                     ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);

@@ -25,6 +25,7 @@ struct Params {
     float* part;       // partial tiles: [grid][maxseg][cp][BM]
     int maxseg;
     int* status;
+    int accumulate;    // 1: out += result (out is read first), 0: out = result
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

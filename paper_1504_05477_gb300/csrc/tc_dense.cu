@@ -287,7 +287,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 dst = p.part + slot * int64_t(CP) * BM + m;
                 stride = BM;
             }
-            if (!whole || row < p.rows_out) {
+            if (whole && p.accumulate) {
+                if (row < p.rows_out) {
+#pragma unroll
+                    for (int j = 0; j < CP; ++j)
+                        if (j < p.c) dst[int64_t(j) * stride] += run[j];
+                }
+            } else if (!whole || row < p.rows_out) {
 #pragma unroll
                 for (int j = 0; j < CP; ++j)
                     if (j < p.c) dst[int64_t(j) * stride] = run[j];
@@ -327,17 +333,20 @@ __global__ void tc_fixup_kernel(Params p, int G) {
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-        if (j + q < p.c) p.out[int64_t(j + q) * p.ldo + row] = s[q];
+        if (j + q < p.c) {
+            float* o = p.out + int64_t(j + q) * p.ldo + row;
+            *o = p.accumulate ? *o + s[q] : s[q];
+        }
 }
 
-// hi/lo split of a thin block (rows x len, row pitch ld).
+// hi/lo split of sign * x for a thin block (rows x len, row pitch ld; sign = +-1).
 __global__ void tf32_split_kernel(const float* __restrict__ x, int rows, int64_t len, int64_t ld,
-                                  float* __restrict__ xh, float* __restrict__ xl) {
+                                  float sign, float* __restrict__ xh, float* __restrict__ xl) {
     const int64_t total = int64_t(rows) * len;
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
          e += int64_t(gridDim.x) * blockDim.x) {
         const int64_t r = e / len, l = e % len;
-        const float v = x[r * ld + l];
+        const float v = sign * x[r * ld + l];
         const float h = tf32_hi(v);
         xh[r * ld + l] = h;
         xl[r * ld + l] = v - h;
@@ -398,7 +407,7 @@ size_t smem_bytes(int cp) {
 // operands do not meet the TMA alignment rules; the caller then uses the SIMT kernel.
 bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda, bool trans, int c,
                     const float* X, int64_t ldx, float* Y, int64_t ldy, float* xh, float* xl,
-                    float* part, int64_t part_cap) {
+                    float* part, int64_t part_cap, bool subtract) {
     using namespace tc;
     if (c < 1) return true;
     if ((reinterpret_cast<uintptr_t>(A) & 15) || ((lda * 4) & 15) || (reinterpret_cast<uintptr_t>(X) & 15) ||
@@ -426,7 +435,8 @@ bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda,
             const int64_t total = int64_t(cg) * len;
             int blocks = int((total + 255) / 256);
             if (blocks > 4 * G) blocks = 4 * G;
-            tf32_split_kernel<<<blocks, 256, 0, ex.stream>>>(Xg, cg, len, ldx, xhg, xlg);
+            tf32_split_kernel<<<blocks, 256, 0, ex.stream>>>(Xg, cg, len, ldx, subtract ? -1.f : 1.f,
+                                                             xhg, xlg);
             ex.launches++;
         }
         CUtensorMap tmXh, tmXl;
@@ -451,6 +461,7 @@ bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda,
         if (int64_t(Gc) * p.maxseg * cp * BM > part_cap) return false;
         p.part = part;
         p.status = ex.status;
+        p.accumulate = subtract ? 1 : 0;
         const size_t smem = smem_bytes(cp);
         cudaError_t err;
         switch (cp) {
