@@ -118,6 +118,10 @@ void csr_transpose(Exec& ex, const int64_t* row_ptr, const int32_t* col, const f
 int64_t seg_upper_bound(int64_t rows, int64_t nnz);
 void csr_segments(Exec& ex, const int64_t* row_ptr, int64_t rows, int64_t* nseg_tmp, int64_t* seg_off,
                   int64_t* seg_row, int64_t* sums);
+// Row pitch (floats) of the row-major staging of X and Y, and the doubles the centring
+// sums need, for c columns.
+int csr_row_pitch(int c);
+int64_t csr_cvec_doubles(int c);
 // Yt (c x ldy thin) = op(A) Xt with op(A) given by its CSR (rows x cols); corr_kind 0: none,
 // 1: subtract mu^T X from every row, 2: subtract mu[row] (1^T X).
 void csr_product(Exec& ex, const int64_t* row_ptr, const int32_t* col, const float* val, int64_t rows,

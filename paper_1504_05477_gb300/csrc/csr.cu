@@ -77,18 +77,35 @@ __global__ void csr_check_ptr(const int64_t* row_ptr, int64_t rows, int64_t nnz,
     }
 }
 
-// One warp per row; runs only when the row pointers passed.
+// Row r holding entry p: the last r with row_ptr[r] <= p (empty rows share offsets).
+__device__ __forceinline__ int64_t row_of(const int64_t* row_ptr, int64_t rows, int64_t p) {
+    int64_t lo = 0, hi = rows;   // row_ptr[lo] <= p < row_ptr[hi] (row_ptr[rows] = nnz > p)
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (row_ptr[mid] <= p) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Column indices in range and strictly increasing within rows; runs only when the row
+// pointers passed.  One warp per run of 512 entries (coalesced), each lane locating its
+// first entry's row by binary search and walking forward.
+constexpr int CHECK_RUN = 512;
 __global__ void csr_check_cols(const int64_t* row_ptr, const int32_t* col, int64_t rows, int64_t cols,
-                               int* status) {
+                               int64_t nnz, int* status) {
     if (bad_input(status)) return;
     const int lane = threadIdx.x & 31;
     bool bad = false;
-    for (int64_t r = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; r < rows;
-         r += (int64_t(gridDim.x) * blockDim.x) >> 5) {
-        const int64_t b = row_ptr[r], e = row_ptr[r + 1];
-        for (int64_t p = b + lane; p < e; p += 32) {
-            const int32_t c = col[p];
-            if (c < 0 || c >= cols || (p > b && col[p - 1] >= c)) bad = true;
+    for (int64_t base = ((blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5) * CHECK_RUN; base < nnz;
+         base += ((int64_t(gridDim.x) * blockDim.x) >> 5) * CHECK_RUN) {
+        const int64_t end = base + CHECK_RUN < nnz ? base + CHECK_RUN : nnz;
+        int64_t q = base + lane;
+        if (q >= end) continue;
+        int64_t r = row_of(row_ptr, rows, q);
+        for (; q < end; q += 32) {
+            while (row_ptr[r + 1] <= q) ++r;
+            const int32_t c = col[q];
+            if (c < 0 || c >= cols || (q > row_ptr[r] && col[q - 1] >= c)) bad = true;
         }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_BADINPUT);
@@ -168,13 +185,27 @@ __global__ void seg_fill(const int64_t* row_ptr, int64_t rows, const int64_t* se
 }
 
 // ------------------------------------------------------------------ SpMM
-// out_rm (rows x c, row-major, ld c) = M X_rm - corr; M in CSR (rows), X_rm (cols x c).
-// corr: kind 0 none; kind 1 (A X centring): subtract cvec[j] from every row;
-//       kind 2 (A^T Y centring): subtract mu[row] * cvec[j].
+// out (rows x xp, row-major) = M X - corr; M in CSR (rows), X (cols x xp, row-major,
+// xp a multiple of 4).  One warp per segment; the columns are covered by q4 = ceil(cb/4)
+// lanes with float4 loads, so a warp advances 32 / q4 non-zeros per step (6 at c = 20)
+// and the per-group sums are added in group order at the end.  Columns are taken in
+// blocks of 128.  corr: kind 0 none; kind 1 (A X centring): subtract cvec[j] from every
+// row; kind 2 (A^T Y centring): subtract mu[row] * cvec[j].
+__device__ __forceinline__ float4 corr4(float4 v, int corr_kind, const double* cvec, const float* mu, int64_t r,
+                                        int j, int c) {
+    if (corr_kind == 0) return v;
+    const double m = corr_kind == 2 ? double(mu[r]) : 1.0;
+    if (j + 0 < c) v.x -= float(m * cvec[j + 0]);
+    if (j + 1 < c) v.y -= float(m * cvec[j + 1]);
+    if (j + 2 < c) v.z -= float(m * cvec[j + 2]);
+    if (j + 3 < c) v.w -= float(m * cvec[j + 3]);
+    return v;
+}
+
 __global__ void spmm_seg_kernel(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                 const float* __restrict__ val, const int64_t* __restrict__ seg_off,
                                 const int64_t* __restrict__ seg_row, int64_t rows, const float* __restrict__ X,
-                                int c, float* __restrict__ out, float* __restrict__ part, int corr_kind,
+                                int c, int xp, float* __restrict__ out, float* __restrict__ part, int corr_kind,
                                 const double* __restrict__ cvec, const float* __restrict__ mu,
                                 const int* status) {
     if (bad_input(status)) return;
@@ -187,9 +218,13 @@ __global__ void spmm_seg_kernel(const int64_t* __restrict__ row_ptr, const int32
         const bool single = seg_off[r + 1] - first == 1;
         const int64_t beg = row_ptr[r] + (s - first) * SEG;
         const int64_t end = min(row_ptr[r + 1], beg + SEG);
-        for (int j0 = 0; j0 < c; j0 += 32) {
-            const int j = j0 + lane;
-            float acc = 0.f;
+        for (int j0 = 0; j0 < c; j0 += 128) {
+            const int cb = c - j0 < 128 ? c - j0 : 128;
+            const int q4 = (cb + 3) >> 2, groups = 32 / q4;
+            const int g = lane / q4, v = lane - g * q4;
+            const bool active = g < groups;
+            const int j = j0 + 4 * v;
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
             for (int64_t p0 = beg; p0 < end; p0 += 32) {
                 const int cnt = int(min(int64_t(32), end - p0));
                 int cc = 0;
@@ -198,21 +233,34 @@ __global__ void spmm_seg_kernel(const int64_t* __restrict__ row_ptr, const int32
                     cc = col[p0 + lane];
                     vv = val[p0 + lane];
                 }
-                for (int t = 0; t < cnt; ++t) {
-                    const int ct = __shfl_sync(0xffffffffu, cc, t);
-                    const float vt = __shfl_sync(0xffffffffu, vv, t);
-                    if (j < c) acc = fmaf(vt, X[int64_t(ct) * c + j], acc);
+                for (int t0 = 0; t0 < cnt; t0 += groups) {
+                    const int t = t0 + g;
+                    const int ct = __shfl_sync(0xffffffffu, cc, t & 31);
+                    const float vt = __shfl_sync(0xffffffffu, vv, t & 31);
+                    if (active && t < cnt) {
+                        const float4 x = *reinterpret_cast<const float4*>(X + int64_t(ct) * xp + j);
+                        acc.x = fmaf(vt, x.x, acc.x);
+                        acc.y = fmaf(vt, x.y, acc.y);
+                        acc.z = fmaf(vt, x.z, acc.z);
+                        acc.w = fmaf(vt, x.w, acc.w);
+                    }
                 }
             }
-            if (j < c) {
-                if (single) {
-                    float v = acc;
-                    if (corr_kind == 1) v -= float(cvec[j]);
-                    else if (corr_kind == 2) v -= float(double(mu[r]) * cvec[j]);
-                    out[r * c + j] = v;
-                } else {
-                    part[s * c + j] = acc;
+            for (int gg = 1; gg < groups; ++gg) {   // group sums in group order
+                const int src = (lane + gg * q4) & 31;
+                const float ox = __shfl_sync(0xffffffffu, acc.x, src);
+                const float oy = __shfl_sync(0xffffffffu, acc.y, src);
+                const float oz = __shfl_sync(0xffffffffu, acc.z, src);
+                const float ow = __shfl_sync(0xffffffffu, acc.w, src);
+                if (g == 0) {
+                    acc.x += ox; acc.y += oy; acc.z += oz; acc.w += ow;
                 }
+            }
+            if (g == 0) {
+                if (single)
+                    *reinterpret_cast<float4*>(out + r * xp + j) = corr4(acc, corr_kind, cvec, mu, r, j, c);
+                else
+                    *reinterpret_cast<float4*>(part + s * xp + j) = acc;
             }
         }
     }
@@ -220,7 +268,7 @@ __global__ void spmm_seg_kernel(const int64_t* __restrict__ row_ptr, const int32
 
 // Rows with several segments: sum the partials in segment order (FP64), then centre.
 __global__ void spmm_fixup_kernel(const int64_t* __restrict__ seg_off, int64_t rows,
-                                  const float* __restrict__ part, int c, float* __restrict__ out,
+                                  const float* __restrict__ part, int c, int xp, float* __restrict__ out,
                                   int corr_kind, const double* __restrict__ cvec, const float* __restrict__ mu) {
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < rows * c;
          e += int64_t(gridDim.x) * blockDim.x) {
@@ -229,19 +277,23 @@ __global__ void spmm_fixup_kernel(const int64_t* __restrict__ seg_off, int64_t r
         const int64_t s0 = seg_off[r], s1 = seg_off[r + 1];
         if (s1 - s0 <= 1) continue;
         double acc = 0.0;
-        for (int64_t s = s0; s < s1; ++s) acc += double(part[s * c + j]);
+        for (int64_t s = s0; s < s1; ++s) acc += double(part[s * xp + j]);
         if (corr_kind == 1) acc -= cvec[j];
         else if (corr_kind == 2) acc -= double(mu[r]) * cvec[j];
-        out[r * c + j] = float(acc);
+        out[r * xp + j] = float(acc);
     }
 }
 
-// cvec[j] = sum_l w[l] * Xt[j][l] (w = mu, or w = NULL for the plain sum 1^T x), FP64.
-__global__ void weighted_sums(const float* __restrict__ Xt, int64_t ld, int64_t len,
-                              const float* __restrict__ w, double* __restrict__ cvec) {
-    const int j = blockIdx.x;
+// cvec[j] = sum_l w[l] * Xt[j][l] (w = mu, or w = NULL for the plain sum 1^T x), FP64:
+// block (j, slice) sums one of WS_SLICES slices, then the slices are added in order.
+constexpr int WS_SLICES = 16;
+__global__ void weighted_sums_part(const float* __restrict__ Xt, int64_t ld, int64_t len,
+                                   const float* __restrict__ w, double* __restrict__ part) {
+    const int j = blockIdx.x, sl = blockIdx.y;
+    const int64_t per = (len + WS_SLICES - 1) / WS_SLICES;
+    const int64_t l0 = sl * per, l1 = l0 + per < len ? l0 + per : len;
     double s = 0.0;
-    for (int64_t l = threadIdx.x; l < len; l += blockDim.x)
+    for (int64_t l = l0 + threadIdx.x; l < l1; l += blockDim.x)
         s += double(Xt[j * ld + l]) * (w ? double(w[l]) : 1.0);
     __shared__ double red[32];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -250,8 +302,16 @@ __global__ void weighted_sums(const float* __restrict__ Xt, int64_t ld, int64_t 
     if (threadIdx.x < 32) {
         double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (threadIdx.x == 0) cvec[j] = t;
+        if (threadIdx.x == 0) part[j * WS_SLICES + sl] = t;
     }
+}
+
+__global__ void weighted_sums_final(const double* __restrict__ part, int c, double* __restrict__ cvec) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= c) return;
+    double s = 0.0;
+    for (int sl = 0; sl < WS_SLICES; ++sl) s += part[j * WS_SLICES + sl];
+    cvec[j] = s;
 }
 
 void exclusive_scan(Exec& ex, const int64_t* in, int64_t n, int64_t* out, int64_t* sums) {
@@ -274,7 +334,8 @@ int grid_for(int64_t work, int per_block, int num_sms) {
 void csr_check(Exec& ex, const int64_t* row_ptr, const int32_t* col, int64_t rows, int64_t cols,
                int64_t nnz, int* status) {
     csr_check_ptr<<<grid_for(rows + 1, 256, ex.num_sms), 256, 0, ex.stream>>>(row_ptr, rows, nnz, status);
-    csr_check_cols<<<grid_for(rows, 8, ex.num_sms), 256, 0, ex.stream>>>(row_ptr, col, rows, cols, status);
+    csr_check_cols<<<grid_for((nnz + CHECK_RUN - 1) / CHECK_RUN, 8, ex.num_sms), 256, 0, ex.stream>>>(
+        row_ptr, col, rows, cols, nnz, status);
     ex.launches += 2;
 }
 
@@ -318,28 +379,33 @@ void csr_segments(Exec& ex, const int64_t* row_ptr, int64_t rows, int64_t* nseg_
     ex.launches += 2;
 }
 
+int csr_row_pitch(int c) { return (c + 3) / 4 * 4; }
+int64_t csr_cvec_doubles(int c) { return int64_t(c) * (WS_SLICES + 1); }
+
 // Y_t (c x ldy, thin) = op(A) X_t with op(A) given by its CSR (rows x cols); centring per
-// corr_kind (see spmm_seg_kernel).  x_rm: cols x c scratch, y_rm: rows x c scratch,
-// part: seg_upper_bound x c scratch, cvec: c doubles.
+// corr_kind (see spmm_seg_kernel).  x_rm: cols x xp scratch, y_rm: rows x xp scratch,
+// part: seg_upper_bound x xp scratch, cvec: csr_cvec_doubles(c) doubles (xp =
+// csr_row_pitch(c)).
 void csr_product(Exec& ex, const int64_t* row_ptr, const int32_t* col, const float* val, int64_t rows,
                  int64_t cols, int64_t nnz, const int64_t* seg_off, const int64_t* seg_row,
                  int64_t nseg_bound, const float* Xt, int64_t ldx, int c, float* Yt, int64_t ldy,
                  float* x_rm, float* y_rm, float* part, int corr_kind, const float* mu, double* cvec) {
     (void)nnz;
-    transpose_in<float>(ex, Xt, 1, c, cols, ldx, x_rm, c);   // x_rm[l][j] = Xt[j][l]
-    if (corr_kind == 1) {        // mu^T X
-        weighted_sums<<<c, 256, 0, ex.stream>>>(Xt, ldx, cols, mu, cvec);
-        ex.launches++;
-    } else if (corr_kind == 2) { // 1^T Y
-        weighted_sums<<<c, 256, 0, ex.stream>>>(Xt, ldx, cols, nullptr, cvec);
-        ex.launches++;
+    const int xp = csr_row_pitch(c);
+    transpose_in<float>(ex, Xt, 1, c, cols, ldx, x_rm, xp);   // x_rm[l][j] = Xt[j][l]
+    if (corr_kind != 0) {   // kind 1: mu^T X; kind 2: 1^T Y
+        double* wpart = cvec + c;
+        weighted_sums_part<<<dim3(unsigned(c), WS_SLICES), 256, 0, ex.stream>>>(
+            Xt, ldx, cols, corr_kind == 1 ? mu : nullptr, wpart);
+        weighted_sums_final<<<(c + 127) / 128, 128, 0, ex.stream>>>(wpart, c, cvec);
+        ex.launches += 2;
     }
     const int warps_per_block = 8;
     spmm_seg_kernel<<<grid_for(nseg_bound, warps_per_block, ex.num_sms), 32 * warps_per_block, 0, ex.stream>>>(
-        row_ptr, col, val, seg_off, seg_row, rows, x_rm, c, y_rm, part, corr_kind, cvec, mu, ex.status);
-    spmm_fixup_kernel<<<grid_for(rows * c, 256, ex.num_sms), 256, 0, ex.stream>>>(seg_off, rows, part, c, y_rm,
+        row_ptr, col, val, seg_off, seg_row, rows, x_rm, c, xp, y_rm, part, corr_kind, cvec, mu, ex.status);
+    spmm_fixup_kernel<<<grid_for(rows * c, 256, ex.num_sms), 256, 0, ex.stream>>>(seg_off, rows, part, c, xp, y_rm,
                                                                                  corr_kind, cvec, mu);
-    transpose_in<float>(ex, y_rm, 1, rows, c, c, Yt, ldy);   // Yt[j][r] = y_rm[r][j]
+    transpose_in<float>(ex, y_rm, 1, rows, c, xp, Yt, ldy);   // Yt[j][r] = y_rm[r][j]
     ex.launches += 2;
 }
 

@@ -251,11 +251,15 @@ __global__ void __launch_bounds__(512) chol_inv_tiled_kernel(const float* __rest
 template <typename T>
 void thin_mm(Exec& ex, const T* A, int64_t rows, int64_t len, int64_t lda, bool trans, int c, const T* X,
              int64_t ldx, T* Y, int64_t ldy, bool subtract, const OrthWs& ws) {
-    if (sizeof(T) == 4 && ws.xh != nullptr &&
-        tc_product_f32(ex, reinterpret_cast<const float*>(A), rows, len, lda, trans, c,
-                       reinterpret_cast<const float*>(X), ldx, reinterpret_cast<float*>(Y), ldy, ws.xh,
-                       ws.xl, ws.tpart, ws.tpart_cap, subtract))
-        return;
+    if (sizeof(T) == 4 && ws.xh != nullptr) {
+        KernelLog* log = ex.klog;   // the kernel log times products with A only
+        ex.klog = nullptr;
+        const bool done = tc_product_f32(ex, reinterpret_cast<const float*>(A), rows, len, lda, trans, c,
+                                         reinterpret_cast<const float*>(X), ldx, reinterpret_cast<float*>(Y),
+                                         ldy, ws.xh, ws.xl, ws.tpart, ws.tpart_cap, subtract);
+        ex.klog = log;
+        if (done) return;
+    }
     GemmDesc g{};
     g.M = c;
     g.N = trans ? len : rows;

@@ -164,10 +164,11 @@ struct CsrLayout {
         seg_row1 = a.take(size_t(segb1) * 8);
         nseg_tmp = a.take(size_t(mx + 1) * 8);
         sums = a.take(size_t(mx / 1024 + 4) * 8);
-        x_rm = a.take(size_t(mx) * c * 4);
-        y_rm = a.take(size_t(mx) * c * 4);
-        part = a.take(size_t(segb0 > segb1 ? segb0 : segb1) * c * 4);
-        cvec = a.take(size_t(c) * 8);
+        const int64_t xp = csr_row_pitch(c);
+        x_rm = a.take(size_t(mx) * xp * 4);
+        y_rm = a.take(size_t(mx) * xp * 4);
+        part = a.take(size_t(segb0 > segb1 ? segb0 : segb1) * xp * 4);
+        cvec = a.take(size_t(csr_cvec_doubles(c)) * 8);
         build = A->t_row_ptr == nullptr;
         if (build) {
             t_rp = a.take(size_t(d + 1) * 8);

@@ -308,7 +308,7 @@ bool tc_product_bf16(Exec& ex, const __nv_bfloat16* A, int64_t n, int64_t d, int
         p.out = Y + int64_t(c0) * ldy;
         p.ldo = ldy;
         const int64_t U = p.tiles * p.cpt;
-        const int Gc = U < G ? int(U) : G;
+        const int Gc = grid_for_units(U, G);
         const int64_t per = (U + Gc - 1) / Gc;
         p.maxseg = int(per / p.cpt + 2);
         if (int64_t(Gc) * p.maxseg * cp * BM > part_cap) return false;

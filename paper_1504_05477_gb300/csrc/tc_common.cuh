@@ -154,6 +154,11 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn();
 bool encode_2d(CUtensorMap* map, CUtensorMapDataType type, const void* ptr, uint64_t inner,
                uint64_t outer, uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer,
                CUtensorMapSwizzle sw);
+// CTAs of a stream-K launch over U units: one per SM, but no fewer than
+// MIN_UNITS_PER_CTA units each (a short contraction then spreads over fewer CTAs and
+// leaves fewer partial tiles to sum).
+constexpr int64_t MIN_UNITS_PER_CTA = 16;
+int grid_for_units(int64_t U, int num_sms);
 // Sum the tiles cut between the G CTAs of a launch into p.out (deterministic order).
 void fixup(Exec& ex, const Params& p, int G);
 // Partial-tile floats a stream-K launch over (rows_out / BM) x (len / kc) units needs.

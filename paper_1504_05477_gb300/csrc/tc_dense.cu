@@ -309,21 +309,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
 }
 
-// Tiles cut between CTAs: out[j][t*BM + m] = sum over the covering CTAs, in CTA order.
-// The CTA owning unit u is floor(((u + 1) G - 1) / U) for the ranges of unit_range.
-__global__ void tc_fixup_kernel(Params p, int G) {
-    // block (t, column group): 128 rows x 8 columns; every output is an independent sum
+// Tiles cut between CTAs: out[j][t*BM + m] = sum over the covering CTAs.  The CTA
+// owning unit u is floor(((u + 1) G - 1) / U) for the ranges of unit_range.  Block
+// (tile, 4 columns), 1024 threads: thread (slot s, row m) sums the CTAs s, s + 8, ...
+// of the covering range, then the 8 slot sums are added in slot order (deterministic).
+constexpr int FIX_SLOTS = 8;
+__global__ void __launch_bounds__(FIX_SLOTS * BM) tc_fixup_kernel(Params p, int G) {
+    __shared__ float red[FIX_SLOTS][4][BM];
     const int64_t t = blockIdx.x;
     const int64_t U = p.tiles * p.cpt;
     const int64_t u0 = t * p.cpt, u1 = (t + 1) * p.cpt - 1;
     const int64_t c_first = ((u0 + 1) * G - 1) / U, c_last = ((u1 + 1) * G - 1) / U;
     if (c_first == c_last) return;   // one CTA wrote the whole tile
-    const int m = threadIdx.x & (BM - 1);
-    const int j = int(blockIdx.y) * 8 + (threadIdx.x >> 7) * 4;   // blockDim = 256: 2 x 4 columns
+    const int m = threadIdx.x % BM, slot = threadIdx.x / BM;
+    const int j = int(blockIdx.y) * 4;
     const int64_t row = t * BM + m;
-    if (row >= p.rows_out) return;
     float s[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int64_t cc = c_first; cc <= c_last; ++cc) {
+    for (int64_t cc = c_first + slot; cc <= c_last; cc += FIX_SLOTS) {
         const int64_t start = (cc * U) / G;
         if (((cc + 1) * U) / G == start) continue;   // a CTA with no units wrote nothing
         const float* src = p.part + ((cc * p.maxseg + (t - start / p.cpt)) * p.cp) * BM + m;
@@ -332,11 +334,17 @@ __global__ void tc_fixup_kernel(Params p, int G) {
             if (j + q < p.c) s[q] += src[int64_t(j + q) * BM];
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (j + q < p.c) {
-            float* o = p.out + int64_t(j + q) * p.ldo + row;
-            *o = p.accumulate ? *o + s[q] : s[q];
-        }
+    for (int q = 0; q < 4; ++q) red[slot][q][m] = s[q];
+    __syncthreads();
+    if (slot != 0 || row >= p.rows_out) return;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (j + q >= p.c) continue;
+        float v = red[0][q][m];
+        for (int k = 1; k < FIX_SLOTS; ++k) v += red[k][q][m];
+        float* o = p.out + int64_t(j + q) * p.ldo + row;
+        *o = p.accumulate ? *o + v : v;
+    }
 }
 
 // hi/lo split of sign * x for a thin block (rows x len, row pitch ld; sign = +-1).
@@ -385,14 +393,19 @@ bool encode_2d(CUtensorMap* map, CUtensorMapDataType type, const void* ptr, uint
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+int grid_for_units(int64_t U, int num_sms) {
+    const int64_t g = U / MIN_UNITS_PER_CTA;
+    return int(g < 1 ? 1 : (g < num_sms ? g : num_sms));
+}
+
 void fixup(Exec& ex, const Params& p, int G) {
-    tc_fixup_kernel<<<dim3(unsigned(p.tiles), unsigned((p.c + 7) / 8)), 2 * BM, 0, ex.stream>>>(p, G);
+    tc_fixup_kernel<<<dim3(unsigned(p.tiles), unsigned((p.c + 3) / 4)), FIX_SLOTS * BM, 0, ex.stream>>>(p, G);
     ex.launches++;
 }
 
 int64_t partial_floats(int64_t rows_out, int64_t len, int kc, int cp, int num_sms) {
     const int64_t tiles = (rows_out + BM - 1) / BM, cpt = (len + kc - 1) / kc;
-    const int64_t U = tiles * cpt, G = U < num_sms ? U : num_sms, per = (U + G - 1) / G;
+    const int64_t U = tiles * cpt, G = grid_for_units(U, num_sms), per = (U + G - 1) / G;
     return G * (per / cpt + 2) * cp * BM;
 }
 
@@ -455,7 +468,7 @@ bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda,
         p.out = Y + int64_t(c0) * ldy;
         p.ldo = ldy;
         const int64_t U = p.tiles * p.cpt;
-        const int Gc = U < G ? int(U) : G;   // every CTA gets at least one unit
+        const int Gc = grid_for_units(U, G);
         const int64_t per = (U + Gc - 1) / Gc;
         p.maxseg = int(per / p.cpt + 2);
         if (int64_t(Gc) * p.maxseg * cp * BM > part_cap) return false;
