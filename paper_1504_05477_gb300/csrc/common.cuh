@@ -154,13 +154,17 @@ struct OrthWs {
     float* tpart = nullptr;       //   stream-K partial tiles
     int64_t tpart_cap = 0;
     int* shifted_flag = nullptr;  // device int: a Cholesky needed a diagonal shift
+    float* fpart = nullptr;       // fused kernel (FP32; nullptr disables it): per-CTA partial
+    int64_t fpart_cap = 0;        //   Grams (floats), the reduced Gram and the barrier words
+    float* fgram = nullptr;
+    unsigned* fbar = nullptr;
 };
 // Byte sizes of those buffers for blocks of c columns, at most mmax earlier columns and
 // lengths up to len_max (pitch up to ld_max).
 struct OrthSizes {
-    size_t partials, g, rfac, ct, xh, tpart;
+    size_t partials, g, rfac, ct, xh, tpart, fpart, fgram, fbar;
     int ldp;
-    int64_t ldc, cap, tcap;
+    int64_t ldc, cap, tcap, fcap;
 };
 OrthSizes orth_sizes(int64_t len_max, int64_t ld_max, int mmax, int c, int elem_bytes, bool tc, int num_sms);
 

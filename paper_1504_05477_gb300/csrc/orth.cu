@@ -140,9 +140,10 @@ __global__ void chol_inv_kernel(const T* __restrict__ G, int64_t ldg, int c, T* 
 // with the pivot d_j = S[j][j].  At the end E = L_unit^{-1} for G = L_unit D L_unit^T,
 // so L^{-1} = D^{-1/2} E.  Same breakdown handling as chol_inv_kernel.
 constexpr int TR = 4, TC = 8;   // register tile: rows x columns per thread (c <= 128: 512 threads)
-__global__ void __launch_bounds__(512) chol_inv_tiled_kernel(const float* __restrict__ G, int64_t ldg, int c,
-                                                             float* __restrict__ P, int64_t ldp, int* status,
-                                                             int* shifted_flag) {
+// Block-wide device routine (needs (c/4)(c/8) threads, all threads of the block call it;
+// G and P may live in global or shared memory).
+__device__ void chol_inv_block(const float* G, int64_t ldg, int c, float* P, int64_t ldp, int* status,
+                               int* shifted_flag) {
     __shared__ float rowS[2][128], rowE[2][128];
     __shared__ double trace_s;
     const int ntc = (c + TC - 1) / TC, ntr = (c + TR - 1) / TR;
@@ -244,6 +245,12 @@ __global__ void __launch_bounds__(512) chol_inv_tiled_kernel(const float* __rest
     }
 }
 
+__global__ void __launch_bounds__(512) chol_inv_tiled_kernel(const float* __restrict__ G, int64_t ldg, int c,
+                                                             float* __restrict__ P, int64_t ldp, int* status,
+                                                             int* shifted_flag) {
+    chol_inv_block(G, ldg, c, P, ldp, status, shifted_flag);
+}
+
 // Thin-block product through the tensor cores when T = float and the operands meet the
 // TMA rules, else the SIMT kernel.  A: rows x len thin (pitch lda); X: c x (len or rows).
 //   trans = false: Y (c x rows)  = (A X^T)^T,  Y[j][r] = sum_l A[r][l] X[j][l]
@@ -295,12 +302,407 @@ void cholqr_pass(Exec& ex, int64_t len, int64_t ld, const T* src, int c, T* dst,
     thin_mm<T>(ex, src, c, len, ld, true, c, P, ws.ldp, dst, ld, false, ws);    // dst = (W R^{-1})^T
 }
 
+
+// ------------------------------------------------------------------ fused orthonormalisation
+// The whole of orth_block for one block in one cooperative launch (FP32; c <= 64,
+// m + c <= 512).  CTA g owns rows [l0, l1) of the tall matrices and streams them through
+// shared memory in chunks of LC; Grams are reduced across CTAs in a fixed order between
+// grid barriers, and the small c x c factorisations are repeated by every CTA.
+//   P1  C1 = Q^T W                                    (projection coefficients)
+//   P2  W' = W - Q C1,  [C2; H] = [Q W']^T W'          (second projection, fused Gram)
+//   P3  R1 = chol(H - C2^T C2)  (Pythagorean: the Gram of W' - Q C2),
+//       W1 = (W' - Q C2) R1^{-1} = [Q W'] [-C2 R1^{-1}; R1^{-1}],  H3 = W1^T W1
+//   P4  Qout = W1 chol(H3)^{-1}
+// i.e. BCGS2 followed by CholeskyQR2, with the second projection and the first
+// Cholesky sharing one Gram pass.
+namespace of {
+
+constexpr int NT = 256;
+constexpr int LC = 32;
+constexpr int LCP = LC + 1;
+constexpr int RMAX = 512;
+constexpr int CMAX = 64;
+constexpr int COEF_FLOATS = 24576;
+constexpr int SLOTS = 8;
+constexpr int MAXG = 160;
+constexpr uint64_t WAIT_NS = 1000000000ull;
+// dynamic shared memory bound over every (m, c) that orth_fused_fits accepts
+constexpr int MAX_DYN_FLOATS = COEF_FLOATS + RMAX * LCP + CMAX * LCP + 2 * CMAX * CMAX + 16;
+
+struct Args {
+    const float* Q;
+    float* W;
+    float* Wtmp;
+    float* Qout;
+    int m, c;
+    int64_t len, ld;
+    float* part;      // grid x round_up((m + c) c, 4)
+    float* gram;      // (m + c) x c
+    unsigned* bar;    // [0] arrivals, [1] abort
+    int* status;
+    int* shifted_flag;
+};
+
+__host__ __device__ inline int r4(int x) { return (x + 3) & ~3; }
+
+struct Layout {
+    int coef, ach, wout, hbuf, pbuf, total;   // float offsets
+    __host__ __device__ Layout(int m, int c) {
+        const int R = m + c;
+        coef = 0;
+        ach = r4(R * r4(c));
+        wout = ach + r4(R * LCP);
+        hbuf = wout + r4(c * LCP);
+        pbuf = hbuf + r4(c * c);
+        total = pbuf + r4(c * c);
+    }
+};
+
+__device__ __forceinline__ uint64_t gtime() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier (all CTAs are co-resident: cooperative launch).  Bounded: after 1 s
+// the CTA flags ST_TIMEOUT and raises the abort word, which releases the others.
+__device__ bool grid_sync(unsigned* bar, unsigned target, int* status) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(&bar[0], 1u);
+        const uint64_t t0 = gtime();
+        int ok = 1;
+        while (*reinterpret_cast<volatile unsigned*>(&bar[0]) < target) {
+            if (*reinterpret_cast<volatile unsigned*>(&bar[1])) { ok = 0; break; }
+            if (gtime() - t0 > WAIT_NS) {
+                atomicOr(status, ST_TIMEOUT);
+                atomicExch(&bar[1], 1u);
+                ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// rows [0, nrows) of a thin block (pitch ld), columns [lb, lb + LC) clipped to l1 -> dst
+__device__ __forceinline__ void load_rows(float* dst, const float* src, int nrows, int64_t ld, int64_t lb,
+                                          int64_t l1) {
+    for (int e = threadIdx.x; e < nrows * LC; e += NT) {
+        const int r = e / LC, l = e % LC;
+        dst[r * LCP + l] = (lb + l < l1) ? src[int64_t(r) * ld + lb + l] : 0.f;
+    }
+}
+
+__device__ __forceinline__ void store_rows(float* dst, const float* src, int nrows, int64_t ld, int64_t lb,
+                                           int64_t l1) {
+    for (int e = threadIdx.x; e < nrows * LC; e += NT) {
+        const int r = e / LC, l = e % LC;
+        if (lb + l < l1) dst[int64_t(r) * ld + lb + l] = src[r * LCP + l];
+    }
+}
+
+// Gram tile of this thread: rows rg + k RS (k < 4) of A, columns j0 .. j0 + TJ - 1 of B.
+struct GramMap {
+    int nj, TJ, RS, rg, j0;
+    __device__ GramMap(int c) {
+        nj = c > 32 ? 2 : 1;
+        TJ = (c + nj - 1) / nj;
+        RS = NT / nj;
+        rg = threadIdx.x / nj;
+        j0 = (threadIdx.x % nj) * TJ;
+    }
+};
+
+__device__ __forceinline__ void gram_acc(float (&acc)[4][32], const GramMap& g, const float* A, int Ra,
+                                         const float* B, int c) {
+    for (int l = 0; l < LC; ++l) {
+        float a[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int r = g.rg + k * g.RS;
+            a[k] = r < Ra ? A[r * LCP + l] : 0.f;
+        }
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+            if (jj < g.TJ && g.j0 + jj < c) {
+                const float b = B[(g.j0 + jj) * LCP + l];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[k][jj] = fmaf(a[k], b, acc[k][jj]);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void gram_write(const float (&acc)[4][32], const GramMap& g, float* dst, int Ra,
+                                           int c) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int r = g.rg + k * g.RS;
+        if (r >= Ra) continue;
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj)
+            if (jj < g.TJ && g.j0 + jj < c) dst[r * c + g.j0 + jj] = acc[k][jj];
+    }
+}
+
+// out[e] = sum over CTAs g (in order) of part[g * ep + e], e < n: this CTA's stripe.
+__device__ void reduce_stripe(const float* part, int G, int n, float* out) {
+    __shared__ double red[SLOTS][32][4];
+    const int ep = r4(n), nq = ep / 4;
+    const int q0 = int(int64_t(blockIdx.x) * nq / G), q1 = int(int64_t(blockIdx.x + 1) * nq / G);
+    const int lane = threadIdx.x & 31, slot = threadIdx.x >> 5;
+    for (int qb = q0; qb < q1; qb += 32) {
+        const int q = qb + lane;
+        double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        if (q < q1) {
+            float4 v[MAXG / SLOTS];
+#pragma unroll
+            for (int i = 0; i < MAXG / SLOTS; ++i) {
+                const int g = slot + i * SLOTS;
+                v[i] = g < G ? __ldcg(reinterpret_cast<const float4*>(part + int64_t(g) * ep) + q)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int i = 0; i < MAXG / SLOTS; ++i) {
+                s0 += v[i].x; s1 += v[i].y; s2 += v[i].z; s3 += v[i].w;
+            }
+        }
+        red[slot][lane][0] = s0; red[slot][lane][1] = s1; red[slot][lane][2] = s2; red[slot][lane][3] = s3;
+        __syncthreads();
+        if (slot == 0 && q < q1) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                double v = red[0][lane][t];
+                for (int k = 1; k < SLOTS; ++k) v += red[k][lane][t];
+                if (4 * q + t < n) out[4 * q + t] = float(v);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// wout[j][l] = (base ? base[j][l] : 0) - sign * sum_{r < Ra} coef[r][j] A[r][l]
+// (warp w: columns w JW .. w JW + JW - 1, lane = l).
+__device__ __forceinline__ void apply_chunk(float* wout, const float* coef, int cs, const float* A, int Ra,
+                                            const float* base, int c, bool subtract) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int JW = r4((c + 7) / 8);
+    const int j0 = w * JW;
+    if (j0 >= c) return;
+    float acc[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) acc[t] = 0.f;
+    for (int r = 0; r < Ra; ++r) {
+        const float a = A[r * LCP + lane];
+        const float4 c0 = *reinterpret_cast<const float4*>(coef + r * cs + j0);
+        acc[0] = fmaf(c0.x, a, acc[0]);
+        acc[1] = fmaf(c0.y, a, acc[1]);
+        acc[2] = fmaf(c0.z, a, acc[2]);
+        acc[3] = fmaf(c0.w, a, acc[3]);
+        if (JW == 8) {
+            const float4 c1 = *reinterpret_cast<const float4*>(coef + r * cs + j0 + 4);
+            acc[4] = fmaf(c1.x, a, acc[4]);
+            acc[5] = fmaf(c1.y, a, acc[5]);
+            acc[6] = fmaf(c1.z, a, acc[6]);
+            acc[7] = fmaf(c1.w, a, acc[7]);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int j = j0 + t;
+        if (t < JW && j < c)
+            wout[j * LCP + lane] = subtract ? base[j * LCP + lane] - acc[t] : acc[t];
+    }
+}
+
+__global__ void __launch_bounds__(NT, 1) orth_fused_kernel(Args a) {
+    extern __shared__ float4 sm4[];
+    float* sm = reinterpret_cast<float*>(sm4);
+    const int m = a.m, c = a.c, R = m + c, cs = r4(c);
+    const Layout L(m, c);
+    float* coef = sm + L.coef;
+    float* ach = sm + L.ach;
+    float* wout = sm + L.wout;
+    float* hbuf = sm + L.hbuf;
+    float* pbuf = sm + L.pbuf;
+    const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+    const int64_t l0 = int64_t(cta) * a.len / G, l1 = int64_t(cta + 1) * a.len / G;
+    unsigned phase = 0;
+    const GramMap gm(c);
+    float acc[4][32];
+    auto zero = [&]() {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) acc[k][jj] = 0.f;
+    };
+    // reduce the partial Grams of Ra x c outputs into a.gram (two grid barriers)
+    auto reduce = [&](int Ra) -> bool {
+        gram_write(acc, gm, a.part + int64_t(cta) * r4(Ra * c), Ra, c);
+        if (!grid_sync(a.bar, ++phase * G, a.status)) return false;
+        reduce_stripe(a.part, G, Ra * c, a.gram);
+        return grid_sync(a.bar, ++phase * G, a.status);
+    };
+
+    // ---- P1: C1 = Q^T W
+    if (m > 0) {
+        zero();
+        for (int64_t lb = l0; lb < l1; lb += LC) {
+            load_rows(ach, a.Q, m, a.ld, lb, l1);
+            load_rows(ach + m * LCP, a.W, c, a.ld, lb, l1);
+            __syncthreads();
+            gram_acc(acc, gm, ach, m, ach + m * LCP, c);
+            __syncthreads();
+        }
+        if (!reduce(m)) return;
+        for (int e = tid; e < m * c; e += NT) coef[(e / c) * cs + e % c] = __ldcg(a.gram + e);
+        __syncthreads();
+    }
+    // ---- P2: W' = W - Q C1 (written back to W), Gram [Q W']^T W'
+    zero();
+    for (int64_t lb = l0; lb < l1; lb += LC) {
+        if (m > 0) load_rows(ach, a.Q, m, a.ld, lb, l1);
+        load_rows(ach + m * LCP, a.W, c, a.ld, lb, l1);
+        __syncthreads();
+        if (m > 0) {
+            apply_chunk(wout, coef, cs, ach, m, ach + m * LCP, c, true);
+            __syncthreads();
+            for (int e = tid; e < c * LC; e += NT) ach[(m + e / LC) * LCP + e % LC] = wout[(e / LC) * LCP + e % LC];
+            store_rows(a.W, wout, c, a.ld, lb, l1);
+            __syncthreads();
+        }
+        gram_acc(acc, gm, ach, R, ach + m * LCP, c);
+        __syncthreads();
+    }
+    if (!reduce(R)) return;
+    // ---- P3: R1 from H - C2^T C2; coefficients [-C2 P1^T; P1^T] with P1 = R1^{-T}
+    for (int e = tid; e < R * c; e += NT) coef[(e / c) * cs + e % c] = __ldcg(a.gram + e);
+    __syncthreads();
+    for (int e = tid; e < c * c; e += NT) {
+        const int i = e / c, j = e % c;
+        float h = coef[(m + i) * cs + j];
+        for (int r = 0; r < m; ++r) h = fmaf(-coef[r * cs + i], coef[r * cs + j], h);
+        hbuf[e] = h;
+    }
+    __syncthreads();
+    chol_inv_block(hbuf, c, c, pbuf, c, a.status, a.shifted_flag);
+    __syncthreads();
+    for (int r = tid; r < m; r += NT) {   // row r of -C2 P1^T, in place
+        float row[CMAX];
+#pragma unroll
+        for (int b = 0; b < CMAX; ++b) row[b] = b < c ? coef[r * cs + b] : 0.f;
+        for (int j = 0; j < c; ++j) {
+            float v = 0.f;
+#pragma unroll
+            for (int b = 0; b < CMAX; ++b)
+                if (b < c) v = fmaf(pbuf[j * c + b], row[b], v);
+            coef[r * cs + j] = -v;
+        }
+    }
+    for (int e = tid; e < c * c; e += NT) {
+        const int b = e / c, j = e % c;
+        coef[(m + b) * cs + j] = pbuf[j * c + b];
+    }
+    __syncthreads();
+    zero();
+    for (int64_t lb = l0; lb < l1; lb += LC) {
+        if (m > 0) load_rows(ach, a.Q, m, a.ld, lb, l1);
+        load_rows(ach + m * LCP, a.W, c, a.ld, lb, l1);
+        __syncthreads();
+        apply_chunk(wout, coef, cs, ach, R, nullptr, c, false);
+        __syncthreads();
+        store_rows(a.Wtmp, wout, c, a.ld, lb, l1);
+        gram_acc(acc, gm, wout, c, wout, c);
+        __syncthreads();
+    }
+    if (!reduce(c)) return;
+    // ---- P4: Qout = P2 W1, P2 = chol(H3)^{-T}
+    for (int e = tid; e < c * c; e += NT) hbuf[e] = __ldcg(a.gram + e);
+    __syncthreads();
+    chol_inv_block(hbuf, c, c, pbuf, c, a.status, a.shifted_flag);
+    __syncthreads();
+    for (int e = tid; e < c * c; e += NT) {
+        const int b = e / c, j = e % c;
+        coef[b * cs + j] = pbuf[j * c + b];
+    }
+    __syncthreads();
+    for (int64_t lb = l0; lb < l1; lb += LC) {
+        load_rows(ach, a.Wtmp, c, a.ld, lb, l1);
+        __syncthreads();
+        apply_chunk(wout, coef, cs, ach, c, nullptr, c, false);
+        __syncthreads();
+        store_rows(a.Qout, wout, c, a.ld, lb, l1);
+        __syncthreads();
+    }
+}
+
+}  // namespace of
+
+bool orth_fused_fits(int m, int c) {
+    const int R = m + c;
+    return c >= 1 && c <= of::CMAX && R <= of::RMAX && R * of::r4(c) <= of::COEF_FLOATS;
+}
+
+// One cooperative launch; false (nothing launched) when it cannot run.
+bool orth_fused(Exec& ex, int64_t len, int64_t ld, const float* Qb, int m, float* W, int c, float* Wtmp,
+                float* Qout, const OrthWs& ws) {
+    if (ws.fpart == nullptr || !orth_fused_fits(m, c)) return false;
+    const of::Layout L(m, c);
+    const size_t smem = size_t(L.total) * sizeof(float);
+    if (L.total > of::MAX_DYN_FLOATS) return false;
+    static int configured_device = -1;
+    static int per_sm = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (configured_device != dev) {
+        if (cudaFuncSetAttribute(of::orth_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(of::MAX_DYN_FLOATS * sizeof(float))) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        configured_device = dev;
+        per_sm = 0;
+    }
+    if (per_sm == 0 &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, of::orth_fused_kernel, of::NT,
+                                                      of::MAX_DYN_FLOATS * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 0;
+    }
+    const int G = ex.num_sms < of::MAXG ? ex.num_sms : of::MAXG;
+    if (per_sm < 1 || int64_t(G) * of::r4((m + c) * c) > ws.fpart_cap) return false;
+    of::Args a;
+    a.Q = Qb; a.W = W; a.Wtmp = Wtmp; a.Qout = Qout;
+    a.m = m; a.c = c; a.len = len; a.ld = ld;
+    a.part = ws.fpart; a.gram = ws.fgram; a.bar = ws.fbar;
+    a.status = ex.status; a.shifted_flag = ws.shifted_flag;
+    cudaMemsetAsync(ws.fbar, 0, 2 * sizeof(unsigned), ex.stream);
+    void* args[] = {&a};
+    if (cudaLaunchCooperativeKernel(reinterpret_cast<void*>(of::orth_fused_kernel), dim3(G), dim3(of::NT), args,
+                                    smem, ex.stream) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    ex.launches++;
+    return true;
+}
+
 }  // namespace
 
 // W (c x ld) against Qb (m x ld): BCGS2 then CholeskyQR2, result in Qout (Qout may be W).
 template <typename T>
 void orth_block(Exec& ex, int64_t len, int64_t ld, const T* Qb, int m, T* W, int c, T* Wtmp, T* Qout,
                 const OrthWs& ws) {
+    if (sizeof(T) == 4 &&
+        orth_fused(ex, len, ld, reinterpret_cast<const float*>(Qb), m, reinterpret_cast<float*>(W), c,
+                   reinterpret_cast<float*>(Wtmp), reinterpret_cast<float*>(Qout), ws))
+        return;
     if (m > 0) {
         T* ct = static_cast<T*>(ws.ct);
         for (int pass = 0; pass < 2; ++pass) {
@@ -333,6 +735,11 @@ OrthSizes orth_sizes(int64_t len_max, int64_t ld_max, int mmax, int c, int elem_
         z.tcap = int64_t(num_sms) * ((tiles + num_sms - 1) / num_sms + 3) * cp * 128;
         z.xh = size_t(c) * ld_max * 4;
         z.tpart = size_t(z.tcap) * 4;
+        const int R = int(mm + c < of::RMAX ? mm + c : of::RMAX);
+        z.fcap = int64_t(of::MAXG) * of::r4(R * c);
+        z.fpart = size_t(z.fcap) * 4;
+        z.fgram = size_t(R) * c * 4;
+        z.fbar = 16;
     }
     return z;
 }

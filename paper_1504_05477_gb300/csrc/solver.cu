@@ -273,7 +273,8 @@ struct Plan {
     bool sparse;
     CsrLayout csr;
     size_t Qt, Bt, QBt, Pit, W, Wtmp, Wb, Wbtmp, part, og, rfac, ct, Rm, JX, lam, nrm, Vt,
-        order, Vk, stat;
+        order, Vk, stat, fpart, fgram, fbar;
+    int64_t fcap;
     int ldp;
     int64_t ldc;
     int64_t part_cap;
@@ -321,6 +322,10 @@ Plan make_plan(const bks_matrix* A, int k, int q_eff, int w, size_t tb, int sms)
     p.og = a.take(on.g);
     p.rfac = a.take(on.rfac);
     p.ct = a.take(on.ct);
+    p.fcap = on.fcap > od.fcap ? on.fcap : od.fcap;
+    p.fpart = a.take(size_t(p.fcap) * 4);
+    p.fgram = a.take(on.fgram > od.fgram ? on.fgram : od.fgram);
+    p.fbar = a.take(16);
     p.Rm = a.take(size_t(w) * w * tb);
     p.JX = a.take(size_t(w) * w * tb);
     p.lam = a.take(size_t(w) * tb);
@@ -485,6 +490,12 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
         ows.xl = pw.xl;
         ows.tpart = pw.tpart;
         ows.tpart_cap = pw.tpart_cap;
+        if (p.fcap > 0) {                            // fused one-launch orthonormalisation
+            ows.fpart = reinterpret_cast<float*>(base + p.fpart);
+            ows.fpart_cap = p.fcap;
+            ows.fgram = reinterpret_cast<float*>(base + p.fgram);
+            ows.fbar = reinterpret_cast<unsigned*>(base + p.fbar);
+        }
     }
     auto orth = [&](int m, T* Qout) {
         const int b = prof.begin();
@@ -910,6 +921,7 @@ bks_status bks_orthonormalize(bks_ctx* ctx, int dtype, int64_t len, int m, int c
     Arena a;
     const size_t o_part = a.take(z.partials), o_g = a.take(z.g), o_rfac = a.take(z.rfac),
                  o_ct = a.take(z.ct), o_xh = a.take(z.xh), o_xl = a.take(z.xh), o_tp = a.take(z.tpart),
+                 o_fp = a.take(z.fpart), o_fg = a.take(z.fgram), o_fb = a.take(z.fbar),
                  o_wtmp = a.take(size_t(c) * ldw * tb), o_stat = a.take(16);
     bks_status s = ensure_ws(ctx, a.off);
     if (s != BKS_OK) return s;
@@ -934,6 +946,10 @@ bks_status bks_orthonormalize(bks_ctx* ctx, int dtype, int64_t len, int m, int c
         ws.xl = reinterpret_cast<float*>(base + o_xl);
         ws.tpart = reinterpret_cast<float*>(base + o_tp);
         ws.tpart_cap = z.tcap;
+        ws.fpart = reinterpret_cast<float*>(base + o_fp);
+        ws.fpart_cap = z.fcap;
+        ws.fgram = reinterpret_cast<float*>(base + o_fg);
+        ws.fbar = reinterpret_cast<unsigned*>(base + o_fb);
     }
     if (dtype == BKS_F64)
         orth_block<double>(ex, len, ldw, static_cast<const double*>(Qb), m, static_cast<double*>(W), c,
