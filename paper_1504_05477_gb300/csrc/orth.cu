@@ -318,16 +318,15 @@ void cholqr_pass(Exec& ex, int64_t len, int64_t ld, const T* src, int c, T* dst,
 namespace of {
 
 constexpr int NT = 256;
-constexpr int LC = 32;
-constexpr int LCP = LC + 1;
+constexpr int LC = 32;           // rows of the tall matrices per chunk (= lanes of the apply)
+constexpr int LCP = LC + 1;      // padded shared row
+constexpr int NB = 2;            // chunk stages (cp.async double buffering)
 constexpr int RMAX = 512;
 constexpr int CMAX = 64;
-constexpr int COEF_FLOATS = 24576;
 constexpr int SLOTS = 8;
 constexpr int MAXG = 160;
 constexpr uint64_t WAIT_NS = 1000000000ull;
-// dynamic shared memory bound over every (m, c) that orth_fused_fits accepts
-constexpr int MAX_DYN_FLOATS = COEF_FLOATS + RMAX * LCP + CMAX * LCP + 2 * CMAX * CMAX + 16;
+constexpr int MAX_DYN_FLOATS = 56 * 1024;   // 224 KB of dynamic shared memory at most
 
 struct Args {
     const float* Q;
@@ -345,16 +344,22 @@ struct Args {
 
 __host__ __device__ inline int r4(int x) { return (x + 3) & ~3; }
 
+// Shared layout (floats).  The small factorisation buffers and the reduction scratch
+// alias the chunk stages: they are used only outside the chunk loops.
 struct Layout {
-    int coef, ach, wout, hbuf, pbuf, total;   // float offsets
+    int coef, ach, wout, hbuf, pbuf, red, total, stage;
     __host__ __device__ Layout(int m, int c) {
         const int R = m + c;
+        stage = r4(R * LCP);
         coef = 0;
         ach = r4(R * r4(c));
-        wout = ach + r4(R * LCP);
-        hbuf = wout + r4(c * LCP);
+        wout = ach + NB * stage;
+        total = wout + r4(c * LCP);
+        hbuf = ach;
         pbuf = hbuf + r4(c * c);
-        total = pbuf + r4(c * c);
+        red = pbuf + r4(c * c);   // SLOTS x 32 x 4 doubles = 2048 floats
+        const int need = red + 2 * SLOTS * 32 * 4;
+        if (need > total) total = need;
     }
 };
 
@@ -390,12 +395,51 @@ __device__ bool grid_sync(unsigned* bar, unsigned target, int* status) {
     return ok_s != 0;
 }
 
-// rows [0, nrows) of a thin block (pitch ld), columns [lb, lb + LC) clipped to l1 -> dst
-__device__ __forceinline__ void load_rows(float* dst, const float* src, int nrows, int64_t ld, int64_t lb,
-                                          int64_t l1) {
-    for (int e = threadIdx.x; e < nrows * LC; e += NT) {
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Stage rows [0, n1) of src1 and [0, n2) of src2 (pitch ld), columns [lb, lb + LC) clipped
+// to l1, into dst rows 0.. and n1.. (zeros past l1).
+__device__ __forceinline__ void issue_rows(float* dst, const float* src1, int n1, const float* src2, int n2,
+                                           int64_t ld, int64_t lb, int64_t l1) {
+    const int n = n1 + n2;
+    for (int e = threadIdx.x; e < n * LC; e += NT) {
         const int r = e / LC, l = e % LC;
-        dst[r * LCP + l] = (lb + l < l1) ? src[int64_t(r) * ld + lb + l] : 0.f;
+        float* d = dst + r * LCP + l;
+        if (lb + l < l1) {
+            const float* src = r < n1 ? src1 + int64_t(r) * ld : src2 + int64_t(r - n1) * ld;
+            cp_async4(d, src + lb + l);
+        } else {
+            *d = 0.f;
+        }
+    }
+    cp_commit();
+}
+
+// for every chunk of [l0, l1): stage it, then body(stage pointer, lb) (double-buffered)
+template <class Body>
+__device__ __forceinline__ void stream_chunks(float* stages, int stage, const float* src1, int n1,
+                                              const float* src2, int n2, int64_t ld, int64_t l0, int64_t l1,
+                                              Body body) {
+    if (l0 >= l1) return;
+    issue_rows(stages, src1, n1, src2, n2, ld, l0, l1);
+    int k = 0;
+    for (int64_t lb = l0; lb < l1; lb += LC, ++k) {
+        if (lb + LC < l1) {
+            issue_rows(stages + ((k + 1) % NB) * stage, src1, n1, src2, n2, ld, lb + LC, l1);
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        __syncthreads();
+        body(stages + (k % NB) * stage, lb);
+        __syncthreads();
     }
 }
 
@@ -407,21 +451,31 @@ __device__ __forceinline__ void store_rows(float* dst, const float* src, int nro
     }
 }
 
-// Gram tile of this thread: rows rg + k RS (k < 4) of A, columns j0 .. j0 + TJ - 1 of B.
+// Gram of Ra rows of A against c rows of B over a chunk.  Thread t: tile t / LS (rows
+// rg, rg + RS, rg + 2 RS, rg + 3 RS; columns j0 .. j0 + TJ - 1), chunk rows l = lsub,
+// lsub + LS, ...; the LS partial tiles are combined by shuffles at the end.
 struct GramMap {
-    int nj, TJ, RS, rg, j0;
-    __device__ GramMap(int c) {
+    int nj, TJ, RS, LS, rg, j0, lsub;
+    bool on;
+    __device__ GramMap(int Ra, int c) {
         nj = c > 32 ? 2 : 1;
         TJ = (c + nj - 1) / nj;
-        RS = NT / nj;
-        rg = threadIdx.x / nj;
-        j0 = (threadIdx.x % nj) * TJ;
+        RS = (Ra + 3) / 4;
+        const int tiles = RS * nj;
+        LS = 1;
+        while (LS < 32 && tiles * LS * 2 <= NT) LS *= 2;
+        const int t = threadIdx.x / LS;
+        lsub = threadIdx.x % LS;
+        on = t < tiles;
+        rg = t / nj;
+        j0 = (t % nj) * TJ;
     }
 };
 
 __device__ __forceinline__ void gram_acc(float (&acc)[4][32], const GramMap& g, const float* A, int Ra,
                                          const float* B, int c) {
-    for (int l = 0; l < LC; ++l) {
+    if (!g.on) return;
+    for (int l = g.lsub; l < LC; l += g.LS) {
         float a[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -439,8 +493,14 @@ __device__ __forceinline__ void gram_acc(float (&acc)[4][32], const GramMap& g, 
     }
 }
 
-__device__ __forceinline__ void gram_write(const float (&acc)[4][32], const GramMap& g, float* dst, int Ra,
-                                           int c) {
+__device__ __forceinline__ void gram_write(float (&acc)[4][32], const GramMap& g, float* dst, int Ra, int c) {
+    for (int off = g.LS / 2; off > 0; off >>= 1) {   // lanes of one tile are adjacent
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) acc[k][jj] += __shfl_xor_sync(0xffffffffu, acc[k][jj], off);
+    }
+    if (!g.on || g.lsub != 0) return;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int r = g.rg + k * g.RS;
@@ -452,8 +512,7 @@ __device__ __forceinline__ void gram_write(const float (&acc)[4][32], const Gram
 }
 
 // out[e] = sum over CTAs g (in order) of part[g * ep + e], e < n: this CTA's stripe.
-__device__ void reduce_stripe(const float* part, int G, int n, float* out) {
-    __shared__ double red[SLOTS][32][4];
+__device__ void reduce_stripe(const float* part, int G, int n, float* out, double* red) {
     const int ep = r4(n), nq = ep / 4;
     const int q0 = int(int64_t(blockIdx.x) * nq / G), q1 = int(int64_t(blockIdx.x + 1) * nq / G);
     const int lane = threadIdx.x & 31, slot = threadIdx.x >> 5;
@@ -473,13 +532,14 @@ __device__ void reduce_stripe(const float* part, int G, int n, float* out) {
                 s0 += v[i].x; s1 += v[i].y; s2 += v[i].z; s3 += v[i].w;
             }
         }
-        red[slot][lane][0] = s0; red[slot][lane][1] = s1; red[slot][lane][2] = s2; red[slot][lane][3] = s3;
+        double* rr = red + (slot * 32 + lane) * 4;
+        rr[0] = s0; rr[1] = s1; rr[2] = s2; rr[3] = s3;
         __syncthreads();
         if (slot == 0 && q < q1) {
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-                double v = red[0][lane][t];
-                for (int k = 1; k < SLOTS; ++k) v += red[k][lane][t];
+                double v = red[lane * 4 + t];
+                for (int k = 1; k < SLOTS; ++k) v += red[(k * 32 + lane) * 4 + t];
                 if (4 * q + t < n) out[4 * q + t] = float(v);
             }
         }
@@ -487,7 +547,7 @@ __device__ void reduce_stripe(const float* part, int G, int n, float* out) {
     }
 }
 
-// wout[j][l] = (base ? base[j][l] : 0) - sign * sum_{r < Ra} coef[r][j] A[r][l]
+// wout[j][l] = (subtract ? base[j][l] : 0) -+ sum_{r < Ra} coef[r][j] A[r][l]
 // (warp w: columns w JW .. w JW + JW - 1, lane = l).
 __device__ __forceinline__ void apply_chunk(float* wout, const float* coef, int cs, const float* A, int Ra,
                                             const float* base, int c, bool subtract) {
@@ -531,10 +591,10 @@ __global__ void __launch_bounds__(NT, 1) orth_fused_kernel(Args a) {
     float* wout = sm + L.wout;
     float* hbuf = sm + L.hbuf;
     float* pbuf = sm + L.pbuf;
+    double* red = reinterpret_cast<double*>(sm + L.red);
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
     const int64_t l0 = int64_t(cta) * a.len / G, l1 = int64_t(cta + 1) * a.len / G;
     unsigned phase = 0;
-    const GramMap gm(c);
     float acc[4][32];
     auto zero = [&]() {
 #pragma unroll
@@ -542,53 +602,71 @@ __global__ void __launch_bounds__(NT, 1) orth_fused_kernel(Args a) {
 #pragma unroll
             for (int jj = 0; jj < 32; ++jj) acc[k][jj] = 0.f;
     };
-    // reduce the partial Grams of Ra x c outputs into a.gram (two grid barriers)
-    auto reduce = [&](int Ra) -> bool {
+    // partial Gram -> ordered cross-CTA sum in a.gram (two grid barriers)
+    auto reduce = [&](const GramMap& gm, int Ra) -> bool {
         gram_write(acc, gm, a.part + int64_t(cta) * r4(Ra * c), Ra, c);
         if (!grid_sync(a.bar, ++phase * G, a.status)) return false;
-        reduce_stripe(a.part, G, Ra * c, a.gram);
+        reduce_stripe(a.part, G, Ra * c, a.gram, red);
         return grid_sync(a.bar, ++phase * G, a.status);
     };
 
     // ---- P1: C1 = Q^T W
     if (m > 0) {
+        const GramMap gm(m, c);
         zero();
-        for (int64_t lb = l0; lb < l1; lb += LC) {
-            load_rows(ach, a.Q, m, a.ld, lb, l1);
-            load_rows(ach + m * LCP, a.W, c, a.ld, lb, l1);
-            __syncthreads();
-            gram_acc(acc, gm, ach, m, ach + m * LCP, c);
-            __syncthreads();
-        }
-        if (!reduce(m)) return;
+        stream_chunks(ach, L.stage, a.Q, m, a.W, c, a.ld, l0, l1, [&](float* st, int64_t) {
+            gram_acc(acc, gm, st, m, st + m * LCP, c);
+        });
+        if (!reduce(gm, m)) return;
         for (int e = tid; e < m * c; e += NT) coef[(e / c) * cs + e % c] = __ldcg(a.gram + e);
         __syncthreads();
     }
     // ---- P2: W' = W - Q C1 (written back to W), Gram [Q W']^T W'
-    zero();
-    for (int64_t lb = l0; lb < l1; lb += LC) {
-        if (m > 0) load_rows(ach, a.Q, m, a.ld, lb, l1);
-        load_rows(ach + m * LCP, a.W, c, a.ld, lb, l1);
-        __syncthreads();
-        if (m > 0) {
-            apply_chunk(wout, coef, cs, ach, m, ach + m * LCP, c, true);
-            __syncthreads();
-            for (int e = tid; e < c * LC; e += NT) ach[(m + e / LC) * LCP + e % LC] = wout[(e / LC) * LCP + e % LC];
-            store_rows(a.W, wout, c, a.ld, lb, l1);
-            __syncthreads();
-        }
-        gram_acc(acc, gm, ach, R, ach + m * LCP, c);
-        __syncthreads();
+    {
+        const GramMap gm(R, c);
+        zero();
+        stream_chunks(ach, L.stage, a.Q, m, a.W, c, a.ld, l0, l1, [&](float* st, int64_t lb) {
+            if (m > 0) {
+                apply_chunk(wout, coef, cs, st, m, st + m * LCP, c, true);
+                __syncthreads();
+                for (int e = tid; e < c * LC; e += NT)
+                    st[(m + e / LC) * LCP + e % LC] = wout[(e / LC) * LCP + e % LC];
+                store_rows(a.W, wout, c, a.ld, lb, l1);
+                __syncthreads();
+            }
+            gram_acc(acc, gm, st, R, st + m * LCP, c);
+        });
+        if (!reduce(gm, R)) return;
     }
-    if (!reduce(R)) return;
     // ---- P3: R1 from H - C2^T C2; coefficients [-C2 P1^T; P1^T] with P1 = R1^{-T}
     for (int e = tid; e < R * c; e += NT) coef[(e / c) * cs + e % c] = __ldcg(a.gram + e);
     __syncthreads();
-    for (int e = tid; e < c * c; e += NT) {
-        const int i = e / c, j = e % c;
-        float h = coef[(m + i) * cs + j];
-        for (int r = 0; r < m; ++r) h = fmaf(-coef[r * cs + i], coef[r * cs + j], h);
-        hbuf[e] = h;
+    {   // H - C2^T C2 by 4 x 4 register tiles
+        const int nt4 = (c + 3) / 4;
+        for (int t = tid; t < nt4 * nt4; t += NT) {
+            const int i0 = (t / nt4) * 4, j0 = (t % nt4) * 4;
+            float h[4][4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) h[x][y] = 0.f;
+            for (int r = 0; r < m; ++r) {
+                const float4 u = *reinterpret_cast<const float4*>(coef + r * cs + i0);
+                const float4 v = *reinterpret_cast<const float4*>(coef + r * cs + j0);
+                const float uu[4] = {u.x, u.y, u.z, u.w}, vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) h[x][y] = fmaf(uu[x], vv[y], h[x][y]);
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) {
+                    const int i = i0 + x, j = j0 + y;
+                    if (i < c && j < c) hbuf[i * c + j] = coef[(m + i) * cs + j] - h[x][y];
+                }
+        }
     }
     __syncthreads();
     chol_inv_block(hbuf, c, c, pbuf, c, a.status, a.shifted_flag);
@@ -610,18 +688,17 @@ __global__ void __launch_bounds__(NT, 1) orth_fused_kernel(Args a) {
         coef[(m + b) * cs + j] = pbuf[j * c + b];
     }
     __syncthreads();
-    zero();
-    for (int64_t lb = l0; lb < l1; lb += LC) {
-        if (m > 0) load_rows(ach, a.Q, m, a.ld, lb, l1);
-        load_rows(ach + m * LCP, a.W, c, a.ld, lb, l1);
-        __syncthreads();
-        apply_chunk(wout, coef, cs, ach, R, nullptr, c, false);
-        __syncthreads();
-        store_rows(a.Wtmp, wout, c, a.ld, lb, l1);
-        gram_acc(acc, gm, wout, c, wout, c);
-        __syncthreads();
+    {
+        const GramMap gm(c, c);
+        zero();
+        stream_chunks(ach, L.stage, a.Q, m, a.W, c, a.ld, l0, l1, [&](float* st, int64_t lb) {
+            apply_chunk(wout, coef, cs, st, R, nullptr, c, false);
+            __syncthreads();
+            store_rows(a.Wtmp, wout, c, a.ld, lb, l1);
+            gram_acc(acc, gm, wout, c, wout, c);
+        });
+        if (!reduce(gm, c)) return;
     }
-    if (!reduce(c)) return;
     // ---- P4: Qout = P2 W1, P2 = chol(H3)^{-T}
     for (int e = tid; e < c * c; e += NT) hbuf[e] = __ldcg(a.gram + e);
     __syncthreads();
@@ -632,21 +709,17 @@ __global__ void __launch_bounds__(NT, 1) orth_fused_kernel(Args a) {
         coef[b * cs + j] = pbuf[j * c + b];
     }
     __syncthreads();
-    for (int64_t lb = l0; lb < l1; lb += LC) {
-        load_rows(ach, a.Wtmp, c, a.ld, lb, l1);
-        __syncthreads();
-        apply_chunk(wout, coef, cs, ach, c, nullptr, c, false);
+    stream_chunks(ach, L.stage, a.Wtmp, c, a.Wtmp, 0, a.ld, l0, l1, [&](float* st, int64_t lb) {
+        apply_chunk(wout, coef, cs, st, c, nullptr, c, false);
         __syncthreads();
         store_rows(a.Qout, wout, c, a.ld, lb, l1);
-        __syncthreads();
-    }
+    });
 }
 
 }  // namespace of
 
 bool orth_fused_fits(int m, int c) {
-    const int R = m + c;
-    return c >= 1 && c <= of::CMAX && R <= of::RMAX && R * of::r4(c) <= of::COEF_FLOATS;
+    return c >= 1 && c <= of::CMAX && m + c <= of::RMAX && of::Layout(m, c).total <= of::MAX_DYN_FLOATS;
 }
 
 // One cooperative launch; false (nothing launched) when it cannot run.
