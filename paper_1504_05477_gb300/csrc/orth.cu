@@ -346,20 +346,32 @@ __host__ __device__ inline int r4(int x) { return (x + 3) & ~3; }
 
 // Shared layout (floats).  The small factorisation buffers and the reduction scratch
 // alias the chunk stages: they are used only outside the chunk loops.
+// Column tile of the Gram (compile-time): 32 for c > 32, else c rounded up to 8.
+__host__ __device__ inline int tile_j(int c) { return c > 32 ? 32 : (c + 7) / 8 * 8; }
+// Zero rows after the real ones, so the column tiles and the 4-row groups run unguarded.
+__host__ __device__ inline int pad_rows(int c) {
+    const int tj = tile_j(c), nj = (c + tj - 1) / tj, p = nj * tj - c;
+    return p > 4 ? p : 4;
+}
 struct Layout {
-    int coef, ach, wout, hbuf, pbuf, red, total, stage;
+    int coef, ach, wout, hbuf, pbuf, c2t, p1t, red, total, stage, pad;
     __host__ __device__ Layout(int m, int c) {
         const int R = m + c;
-        stage = r4(R * LCP);
+        pad = pad_rows(c);
+        stage = r4((R + pad) * LCP);
         coef = 0;
         ach = r4(R * r4(c));
-        wout = ach + NB * stage;
-        total = wout + r4(c * LCP);
+        // scratch used outside the chunk loops, aliasing the stages
         hbuf = ach;
         pbuf = hbuf + r4(c * c);
-        red = pbuf + r4(c * c);   // SLOTS x 32 x 4 doubles = 2048 floats
-        const int need = red + 2 * SLOTS * 32 * 4;
-        if (need > total) total = need;
+        c2t = pbuf + r4(c * c);
+        p1t = c2t + r4(m * c);
+        red = ach;                 // SLOTS x 32 x 4 doubles = 2048 floats
+        int scratch_end = p1t + r4(c * r4(c));
+        if (red + 2 * SLOTS * 32 * 4 > scratch_end) scratch_end = red + 2 * SLOTS * 32 * 4;
+        wout = ach + NB * stage;
+        if (scratch_end > wout) wout = scratch_end;
+        total = wout + r4((c + pad) * LCP);
     }
 };
 
@@ -453,13 +465,14 @@ __device__ __forceinline__ void store_rows(float* dst, const float* src, int nro
 
 // Gram of Ra rows of A against c rows of B over a chunk.  Thread t: tile t / LS (rows
 // rg, rg + RS, rg + 2 RS, rg + 3 RS; columns j0 .. j0 + TJ - 1), chunk rows l = lsub,
-// lsub + LS, ...; the LS partial tiles are combined by shuffles at the end.
+// lsub + LS, ...; the LS partial tiles are combined by shuffles at the end.  Rows past
+// Ra and columns past c read zero padding or rows whose results are discarded.
+template <int TJ>
 struct GramMap {
-    int nj, TJ, RS, LS, rg, j0, lsub;
+    int RS, LS, rg, j0, lsub;
     bool on;
     __device__ GramMap(int Ra, int c) {
-        nj = c > 32 ? 2 : 1;
-        TJ = (c + nj - 1) / nj;
+        const int nj = (c + TJ - 1) / TJ;
         RS = (Ra + 3) / 4;
         const int tiles = RS * nj;
         LS = 1;
@@ -472,33 +485,34 @@ struct GramMap {
     }
 };
 
-__device__ __forceinline__ void gram_acc(float (&acc)[4][32], const GramMap& g, const float* A, int Ra,
-                                         const float* B, int c) {
+template <int TJ>
+__device__ __forceinline__ void gram_acc(float (&acc)[4][TJ], const GramMap<TJ>& g, const float* A,
+                                         const float* B) {
     if (!g.on) return;
+    const float* a0 = A + g.rg * LCP;
+    const float* b0 = B + g.j0 * LCP;
+    const int rs = g.RS * LCP;
     for (int l = g.lsub; l < LC; l += g.LS) {
-        float a[4];
+        float a[4], b[TJ];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int r = g.rg + k * g.RS;
-            a[k] = r < Ra ? A[r * LCP + l] : 0.f;
-        }
+        for (int k = 0; k < 4; ++k) a[k] = a0[k * rs + l];
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
-            if (jj < g.TJ && g.j0 + jj < c) {
-                const float b = B[(g.j0 + jj) * LCP + l];
+        for (int jj = 0; jj < TJ; ++jj) b[jj] = b0[jj * LCP + l];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) acc[k][jj] = fmaf(a[k], b, acc[k][jj]);
-            }
-        }
+        for (int jj = 0; jj < TJ; ++jj)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[k][jj] = fmaf(a[k], b[jj], acc[k][jj]);
     }
 }
 
-__device__ __forceinline__ void gram_write(float (&acc)[4][32], const GramMap& g, float* dst, int Ra, int c) {
+template <int TJ>
+__device__ __forceinline__ void gram_write(float (&acc)[4][TJ], const GramMap<TJ>& g, float* dst, int Ra,
+                                           int c) {
     for (int off = g.LS / 2; off > 0; off >>= 1) {   // lanes of one tile are adjacent
 #pragma unroll
         for (int k = 0; k < 4; ++k)
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj) acc[k][jj] += __shfl_xor_sync(0xffffffffu, acc[k][jj], off);
+            for (int jj = 0; jj < TJ; ++jj) acc[k][jj] += __shfl_xor_sync(0xffffffffu, acc[k][jj], off);
     }
     if (!g.on || g.lsub != 0) return;
 #pragma unroll
@@ -506,8 +520,8 @@ __device__ __forceinline__ void gram_write(float (&acc)[4][32], const GramMap& g
         const int r = g.rg + k * g.RS;
         if (r >= Ra) continue;
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj)
-            if (jj < g.TJ && g.j0 + jj < c) dst[r * c + g.j0 + jj] = acc[k][jj];
+        for (int jj = 0; jj < TJ; ++jj)
+            if (g.j0 + jj < c) dst[r * c + g.j0 + jj] = acc[k][jj];
     }
 }
 
@@ -558,6 +572,7 @@ __device__ __forceinline__ void apply_chunk(float* wout, const float* coef, int 
     float acc[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) acc[t] = 0.f;
+#pragma unroll 4
     for (int r = 0; r < Ra; ++r) {
         const float a = A[r * LCP + lane];
         const float4 c0 = *reinterpret_cast<const float4*>(coef + r * cs + j0);
@@ -581,6 +596,7 @@ __device__ __forceinline__ void apply_chunk(float* wout, const float* coef, int 
     }
 }
 
+template <int TJ>
 __global__ void __launch_bounds__(NT, 1) orth_fused_kernel(Args a) {
     extern __shared__ float4 sm4[];
     float* sm = reinterpret_cast<float*>(sm4);
@@ -592,18 +608,24 @@ __global__ void __launch_bounds__(NT, 1) orth_fused_kernel(Args a) {
     float* hbuf = sm + L.hbuf;
     float* pbuf = sm + L.pbuf;
     double* red = reinterpret_cast<double*>(sm + L.red);
+    float* c2t = sm + L.c2t;
+    float* p1t = sm + L.p1t;
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
     const int64_t l0 = int64_t(cta) * a.len / G, l1 = int64_t(cta + 1) * a.len / G;
     unsigned phase = 0;
-    float acc[4][32];
+    float acc[4][TJ];
     auto zero = [&]() {
 #pragma unroll
         for (int k = 0; k < 4; ++k)
 #pragma unroll
-            for (int jj = 0; jj < 32; ++jj) acc[k][jj] = 0.f;
+            for (int jj = 0; jj < TJ; ++jj) acc[k][jj] = 0.f;
     };
+    // zero padding rows of the chunk stages and of wout (never written afterwards)
+    for (int s2 = 0; s2 < NB; ++s2)
+        for (int e = tid; e < L.pad * LCP; e += NT) ach[s2 * L.stage + R * LCP + e] = 0.f;
+    for (int e = tid; e < L.pad * LCP; e += NT) wout[c * LCP + e] = 0.f;
     // partial Gram -> ordered cross-CTA sum in a.gram (two grid barriers)
-    auto reduce = [&](const GramMap& gm, int Ra) -> bool {
+    auto reduce = [&](const GramMap<TJ>& gm, int Ra) -> bool {
         gram_write(acc, gm, a.part + int64_t(cta) * r4(Ra * c), Ra, c);
         if (!grid_sync(a.bar, ++phase * G, a.status)) return false;
         reduce_stripe(a.part, G, Ra * c, a.gram, red);
@@ -612,10 +634,10 @@ __global__ void __launch_bounds__(NT, 1) orth_fused_kernel(Args a) {
 
     // ---- P1: C1 = Q^T W
     if (m > 0) {
-        const GramMap gm(m, c);
+        const GramMap<TJ> gm(m, c);
         zero();
         stream_chunks(ach, L.stage, a.Q, m, a.W, c, a.ld, l0, l1, [&](float* st, int64_t) {
-            gram_acc(acc, gm, st, m, st + m * LCP, c);
+            gram_acc<TJ>(acc, gm, st, st + m * LCP);
         });
         if (!reduce(gm, m)) return;
         for (int e = tid; e < m * c; e += NT) coef[(e / c) * cs + e % c] = __ldcg(a.gram + e);
@@ -623,7 +645,7 @@ __global__ void __launch_bounds__(NT, 1) orth_fused_kernel(Args a) {
     }
     // ---- P2: W' = W - Q C1 (written back to W), Gram [Q W']^T W'
     {
-        const GramMap gm(R, c);
+        const GramMap<TJ> gm(R, c);
         zero();
         stream_chunks(ach, L.stage, a.Q, m, a.W, c, a.ld, l0, l1, [&](float* st, int64_t lb) {
             if (m > 0) {
@@ -634,7 +656,7 @@ __global__ void __launch_bounds__(NT, 1) orth_fused_kernel(Args a) {
                 store_rows(a.W, wout, c, a.ld, lb, l1);
                 __syncthreads();
             }
-            gram_acc(acc, gm, st, R, st + m * LCP, c);
+            gram_acc<TJ>(acc, gm, st, st + m * LCP);
         });
         if (!reduce(gm, R)) return;
     }
@@ -671,31 +693,61 @@ __global__ void __launch_bounds__(NT, 1) orth_fused_kernel(Args a) {
     __syncthreads();
     chol_inv_block(hbuf, c, c, pbuf, c, a.status, a.shifted_flag);
     __syncthreads();
-    for (int r = tid; r < m; r += NT) {   // row r of -C2 P1^T, in place
-        float row[CMAX];
-#pragma unroll
-        for (int b = 0; b < CMAX; ++b) row[b] = b < c ? coef[r * cs + b] : 0.f;
-        for (int j = 0; j < c; ++j) {
-            float v = 0.f;
-#pragma unroll
-            for (int b = 0; b < CMAX; ++b)
-                if (b < c) v = fmaf(pbuf[j * c + b], row[b], v);
-            coef[r * cs + j] = -v;
-        }
+    // E = -C2 P1^T (m x c) as an apply over the transposed C2: lanes run over rows r
+    for (int e = tid; e < m * c; e += NT) {
+        const int r = e / c, b = e % c;
+        c2t[b * m + r] = coef[r * cs + b];
     }
-    for (int e = tid; e < c * c; e += NT) {
-        const int b = e / c, j = e % c;
-        coef[(m + b) * cs + j] = pbuf[j * c + b];
+    for (int e = tid; e < c * cs; e += NT) {
+        const int b = e / cs, j = e % cs;
+        p1t[e] = j < c ? pbuf[j * c + b] : 0.f;
     }
     __syncthreads();
     {
-        const GramMap gm(c, c);
+        const int lane = tid & 31, w = tid >> 5;
+        const int JW = r4((c + 7) / 8), j0 = w * JW;
+        if (j0 < c)
+            for (int r0 = 0; r0 < m; r0 += 32) {
+                const int r = r0 + lane;
+                float e8[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) e8[t] = 0.f;
+                if (r < m) {
+#pragma unroll 4
+                    for (int b = 0; b < c; ++b) {
+                        const float x = c2t[b * m + r];
+                        const float4 p0 = *reinterpret_cast<const float4*>(p1t + b * cs + j0);
+                        e8[0] = fmaf(x, p0.x, e8[0]);
+                        e8[1] = fmaf(x, p0.y, e8[1]);
+                        e8[2] = fmaf(x, p0.z, e8[2]);
+                        e8[3] = fmaf(x, p0.w, e8[3]);
+                        if (JW == 8) {
+                            const float4 p1 = *reinterpret_cast<const float4*>(p1t + b * cs + j0 + 4);
+                            e8[4] = fmaf(x, p1.x, e8[4]);
+                            e8[5] = fmaf(x, p1.y, e8[5]);
+                            e8[6] = fmaf(x, p1.z, e8[6]);
+                            e8[7] = fmaf(x, p1.w, e8[7]);
+                        }
+                    }
+#pragma unroll
+                    for (int t = 0; t < 8; ++t)
+                        if (t < JW && j0 + t < c) coef[r * cs + j0 + t] = -e8[t];
+                }
+            }
+    }
+    for (int e = tid; e < c * c; e += NT) {
+        const int b = e / c, j = e % c;
+        coef[(m + b) * cs + j] = p1t[b * cs + j];
+    }
+    __syncthreads();
+    {
+        const GramMap<TJ> gm(c, c);
         zero();
         stream_chunks(ach, L.stage, a.Q, m, a.W, c, a.ld, l0, l1, [&](float* st, int64_t lb) {
             apply_chunk(wout, coef, cs, st, R, nullptr, c, false);
             __syncthreads();
             store_rows(a.Wtmp, wout, c, a.ld, lb, l1);
-            gram_acc(acc, gm, wout, c, wout, c);
+            gram_acc<TJ>(acc, gm, wout, wout);
         });
         if (!reduce(gm, c)) return;
     }
@@ -729,27 +781,28 @@ bool orth_fused(Exec& ex, int64_t len, int64_t ld, const float* Qb, int m, float
     const of::Layout L(m, c);
     const size_t smem = size_t(L.total) * sizeof(float);
     if (L.total > of::MAX_DYN_FLOATS) return false;
-    static int configured_device = -1;
-    static int per_sm = 0;
+    const int tj = of::tile_j(c);
+    void* fn = tj == 8    ? reinterpret_cast<void*>(of::orth_fused_kernel<8>)
+               : tj == 16 ? reinterpret_cast<void*>(of::orth_fused_kernel<16>)
+               : tj == 24 ? reinterpret_cast<void*>(of::orth_fused_kernel<24>)
+                          : reinterpret_cast<void*>(of::orth_fused_kernel<32>);
+    static int configured_device[4] = {-1, -1, -1, -1};
+    static int per_sm[4] = {0, 0, 0, 0};
+    const int ti = tj / 8 - 1;
     int dev = 0;
     cudaGetDevice(&dev);
-    if (configured_device != dev) {
-        if (cudaFuncSetAttribute(of::orth_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(of::MAX_DYN_FLOATS * sizeof(float))) != cudaSuccess) {
+    if (configured_device[ti] != dev) {
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(of::MAX_DYN_FLOATS * sizeof(float))) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[ti], fn, of::NT,
+                                                          of::MAX_DYN_FLOATS * sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }
-        configured_device = dev;
-        per_sm = 0;
-    }
-    if (per_sm == 0 &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, of::orth_fused_kernel, of::NT,
-                                                      of::MAX_DYN_FLOATS * sizeof(float)) != cudaSuccess) {
-        cudaGetLastError();
-        per_sm = 0;
+        configured_device[ti] = dev;
     }
     const int G = ex.num_sms < of::MAXG ? ex.num_sms : of::MAXG;
-    if (per_sm < 1 || int64_t(G) * of::r4((m + c) * c) > ws.fpart_cap) return false;
+    if (per_sm[ti] < 1 || int64_t(G) * of::r4((m + c) * c) > ws.fpart_cap) return false;
     of::Args a;
     a.Q = Qb; a.W = W; a.Wtmp = Wtmp; a.Qout = Qout;
     a.m = m; a.c = c; a.len = len; a.ld = ld;
@@ -757,8 +810,7 @@ bool orth_fused(Exec& ex, int64_t len, int64_t ld, const float* Qb, int m, float
     a.status = ex.status; a.shifted_flag = ws.shifted_flag;
     cudaMemsetAsync(ws.fbar, 0, 2 * sizeof(unsigned), ex.stream);
     void* args[] = {&a};
-    if (cudaLaunchCooperativeKernel(reinterpret_cast<void*>(of::orth_fused_kernel), dim3(G), dim3(of::NT), args,
-                                    smem, ex.stream) != cudaSuccess) {
+    if (cudaLaunchCooperativeKernel(fn, dim3(G), dim3(of::NT), args, smem, ex.stream) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
