@@ -144,7 +144,8 @@ constexpr int TR = 4, TC = 8;   // register tile: rows x columns per thread (c <
 // G and P may live in global or shared memory).
 __device__ void chol_inv_block(const float* G, int64_t ldg, int c, float* P, int64_t ldp, int* status,
                                int* shifted_flag) {
-    __shared__ float rowS[2][128], rowE[2][128];
+    __shared__ __align__(16) float rowS[2][128];
+    __shared__ __align__(16) float rowE[2][128];
     __shared__ double trace_s;
     const int ntc = (c + TC - 1) / TC, ntr = (c + TR - 1) / TR;
     const int tid = threadIdx.x;
@@ -204,18 +205,29 @@ __device__ void chol_inv_block(const float* G, int64_t ldg, int c, float* P, int
                 break;
             }
             if (!active || r0 + TR - 1 < j) continue;   // rows of this tile are all done
+            // branch-free update: row j of S and E read once (c0 is a multiple of 8), rows
+            // at or above the pivot get a zero multiplier, columns pick S (l > j) or E
             const float inv = 1.f / d;
+            const float4 sa = *reinterpret_cast<const float4*>(&rowS[par][c0]);
+            const float4 sb = *reinterpret_cast<const float4*>(&rowS[par][c0 + 4]);
+            const float4 ea = *reinterpret_cast<const float4*>(&rowE[par][c0]);
+            const float4 eb = *reinterpret_cast<const float4*>(&rowE[par][c0 + 4]);
+            const float4 fr = *reinterpret_cast<const float4*>(&rowS[par][r0]);
+            const float rsv[TC] = {sa.x, sa.y, sa.z, sa.w, sb.x, sb.y, sb.z, sb.w};
+            const float rev[TC] = {ea.x, ea.y, ea.z, ea.w, eb.x, eb.y, eb.z, eb.w};
+            const float fv[TR] = {fr.x, fr.y, fr.z, fr.w};
 #pragma unroll
             for (int a = 0; a < TR; ++a) {
                 const int i = r0 + a;
-                if (i == j) dpiv[a] = d;
-                if (i <= j) continue;
-                const float f = rowS[par][i] * inv;   // S[i][j] = S[j][i]
+                dpiv[a] = (i == j) ? d : dpiv[a];
+                const float f = (i > j) ? fv[a] * inv : 0.f;   // S[i][j] = S[j][i]
 #pragma unroll
                 for (int b = 0; b < TC; ++b) {
-                    const int l = c0 + b;
-                    if (l > j) s[a][b] = fmaf(-f, rowS[par][l], s[a][b]);
-                    else e[a][b] = fmaf(-f, rowE[par][l], e[a][b]);
+                    const bool right = c0 + b > j;
+                    const float us = fmaf(-f, rsv[b], s[a][b]);
+                    const float ue = fmaf(-f, rev[b], e[a][b]);
+                    s[a][b] = right ? us : s[a][b];
+                    e[a][b] = right ? e[a][b] : ue;
                 }
             }
         }
