@@ -210,6 +210,56 @@ bks_status bks_sym_eig(bks_ctx* ctx, int dtype, int w, const void* M, int64_t ld
 
 /* ---- allocation-free variant ------------------------------------------------------ */
 
+/* Block Krylov on a batch of independent matrices (As[0..batch), each dense or CSR, of
+ * any shapes), the same k, q and opts for all: Zs[i] (n_i x k), sigmas[i] (k) and, if Vs
+ * is non-NULL, Vs[i] (d_i x k), device buffers as for bks_block_krylov.  seeds[i] (NULL:
+ * seed i) or pis[i] (NULL array, or NULL entries: generate from the seed) give the start
+ * blocks.  The solves run on up to 8 streams of the context (created on first use), so
+ * several are in flight at once; the batch is ordered after the work already on the
+ * context's stream, and later work on that stream after the batch.  statuses[i] (host,
+ * may be NULL) receives each solve's status; the return value is the first error, else
+ * BKS_WARN_DEFLATED if any solve was capped, else BKS_OK.  stats (may be NULL) sums
+ * launches, product bytes and flops over the batch.  Synchronises the streams. */
+bks_status bks_block_krylov_batched(bks_ctx* ctx, int batch, const bks_matrix* As, int k, int q,
+                                    const uint64_t* seeds, const void* const* pis, void* const* Zs,
+                                    void* const* sigmas, void* const* Vs, const bks_opts* opts,
+                                    bks_stats* stats, bks_status* statuses);
+
+/* Krylov width w of a solve: k(q_eff + 1) for Block Krylov (method 0; q capped so that
+ * w <= min(n, d), Sec. 4), k for Simultaneous Iteration (method 1).  0 for bad sizes. */
+int bks_krylov_width(int64_t n, int64_t d, int k, int q, int method);
+
+/* All w Ritz triplets of a solve (method 0: Algorithm 2, 1: Algorithm 1) instead of the
+ * top k: U (n x w, row-major; column j = Q ubar_j, Sec. 4), sigma (w, descending) and V
+ * (d x w, row-major; v_j = A^T u_j / sigma_j).  The first k columns are bks_block_krylov's
+ * Z and V.  w = bks_krylov_width(n, d, k, q, method).  Dense or CSR A, FP32 or FP64;
+ * errors as for bks_block_krylov.  This is the forward state that bks_backward needs. */
+bks_status bks_ritz_triplets(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
+                             const void* pi, int method, void* U, void* sigma, void* V,
+                             const bks_opts* opts, bks_stats* stats);
+
+/* Gradient of a loss through Sigma_k and A_k = Z Z^T A with respect to A, from the w Ritz
+ * triplets (U n x w, sigma w, V d x w, row-major, as written by bks_ritz_triplets).  No
+ * counterpart in the paper, which does not differentiate its outputs.  g_sigma (k,
+ * device, may be NULL) is dL/dSigma_k, G (n x d row-major, device, may be NULL) is
+ * dL/dA_k; dA (n x d row-major) receives
+ *   U_k diag(g_sigma) V_k^T + U_k U_k^T G + sum_{i<=k<j<=w} c_ij (s_i u_j v_i^T + s_j u_i v_j^T)
+ *   + (I - U_w U_w^T) G V_k V_k^T,   c_ij = (s_i u_j^T G v_i + s_j u_i^T G v_j) / (s_i^2 - s_j^2),
+ * with c_ij = 0 where s_i^2 - s_j^2 <= gap_tau s_1^2 (gap_tau <= 0: 1e-10 for FP64, 1e-6
+ * for FP32).  Exact when the Krylov space contains range(A).  dtype BKS_F32 or BKS_F64
+ * for every array.  BKS_ERR_INVALID_ARG when both upstream gradients are NULL.
+ * Synchronises the context's stream. */
+bks_status bks_backward(bks_ctx* ctx, int dtype, int64_t n, int64_t d, int k, int w,
+                        const void* U, const void* sigma, const void* V, const void* g_sigma,
+                        const void* G, void* dA, double gap_tau);
+
+/* out (n x d row-major) = U_r diag(sigma_r) V_r^T with the first r columns of U (n x ldu)
+ * and V (d x ldv), row-major, dtype BKS_F32 or BKS_F64: the rank-r approximation
+ * A_r = Z Z^T A of a solve (Z = U_r, A^T Z = V_r diag(sigma_r)).  Synchronises the
+ * context's stream. */
+bks_status bks_low_rank(bks_ctx* ctx, int dtype, int64_t n, int64_t d, int r, const void* U,
+                        int64_t ldu, const void* sigma, const void* V, int64_t ldv, void* out);
+
 /* bks_sym_eig without any device allocation.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory when they call, for
  * example code running where cudaMalloc's implicit device synchronisation is not

@@ -15,6 +15,7 @@ from . import _binding as B
 from ._binding import BksError, BksMatrix, BksOpts, BksStats  # noqa: F401
 
 __all__ = ["block_krylov", "simul_iter", "matmul", "orthonormalize", "sym_eig", "gen_pi", "CsrMatrix",
+           "ritz_triplets", "low_rank", "backward", "rand_svd", "krylov_width", "block_krylov_batched",
            "gen_pi_host", "Context", "context", "dense_matrix", "BksError", "lib_path"]
 
 
@@ -294,3 +295,153 @@ def gen_pi_host(seed, d, k):
                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
             None, "bks_gen_pi_host")
     return out
+
+
+# ---------------------------------------------------------------------- differentiation
+def krylov_width(n, d, k, q, method="bki"):
+    """Number of Ritz triplets of a solve: k(q_eff + 1) for Block Krylov, k for SI."""
+    return int(B.load().bks_krylov_width(int(n), int(d), int(k), int(q), 0 if method == "bki" else 1))
+
+
+def ritz_triplets(a, k, q, seed=0, pi=None, method="bki", precision="auto", **kw):
+    """All w Ritz triplets of a solve (bks_ritz_triplets): U (n x w), sigma (w), V (d x w);
+    the first k are the solve's Z, Sigma_k and V_k."""
+    torch = _torch()
+    mat, dev, odt = _as_bks(a, precision)
+    ctx = context(dev)
+    n, d = mat.n, mat.d
+    w = krylov_width(n, d, k, q, method)
+    if w < 1:
+        raise ValueError("bad sizes")
+    u = torch.empty((n, w), dtype=odt, device=dev)
+    s = torch.empty((w,), dtype=odt, device=dev)
+    v = torch.empty((d, w), dtype=odt, device=dev)
+    if pi is not None and (pi.shape != (d, k) or pi.dtype != odt or not pi.is_contiguous()):
+        raise ValueError(f"pi must be a contiguous {d}x{k} {odt} tensor")
+    opts = _opts(precision=precision, **kw)
+    st = BksStats()
+    status = ctx.lib.bks_ritz_triplets(ctx.ptr, ctypes.byref(mat), int(k), int(q),
+                                       ctypes.c_uint64(seed & (2**64 - 1)),
+                                       ctypes.c_void_p(pi.data_ptr()) if pi is not None else None,
+                                       0 if method == "bki" else 1, ctypes.c_void_p(u.data_ptr()),
+                                       ctypes.c_void_p(s.data_ptr()), ctypes.c_void_p(v.data_ptr()),
+                                       ctypes.byref(opts), ctypes.byref(st))
+    B.check(status, ctx.ptr, "bks_ritz_triplets")
+    return u, s, v
+
+
+def low_rank(u, s, v, r=None):
+    """U_r diag(s_r) V_r^T (bks_low_rank) for row-major U (n x w) and V (d x w)."""
+    torch = _torch()
+    r = s.shape[0] if r is None else int(r)
+    u, s, v = u.contiguous(), s.contiguous(), v.contiguous()
+    ctx = context(u.device)
+    out = torch.empty((u.shape[0], v.shape[0]), dtype=u.dtype, device=u.device)
+    B.check(ctx.lib.bks_low_rank(ctx.ptr, _dtype_code(u.dtype), u.shape[0], v.shape[0], r,
+                                 ctypes.c_void_p(u.data_ptr()), u.stride(0), ctypes.c_void_p(s.data_ptr()),
+                                 ctypes.c_void_p(v.data_ptr()), v.stride(0), ctypes.c_void_p(out.data_ptr())),
+            ctx.ptr, "bks_low_rank")
+    return out
+
+
+def backward(u, s, v, k, g_sigma=None, g_ak=None, gap_tau=0.0):
+    """dL/dA from the Ritz triplets and the upstream gradients of Sigma_k and A_k
+    (bks_backward)."""
+    torch = _torch()
+    u, s, v = u.contiguous(), s.contiguous(), v.contiguous()
+    n, w = u.shape
+    d = v.shape[0]
+    ctx = context(u.device)
+    da = torch.empty((n, d), dtype=u.dtype, device=u.device)
+    gs = g_sigma.contiguous().to(u.dtype) if g_sigma is not None else None
+    ga = g_ak.contiguous().to(u.dtype) if g_ak is not None else None
+    B.check(ctx.lib.bks_backward(ctx.ptr, _dtype_code(u.dtype), n, d, int(k), w,
+                                 ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(s.data_ptr()),
+                                 ctypes.c_void_p(v.data_ptr()),
+                                 ctypes.c_void_p(gs.data_ptr()) if gs is not None else None,
+                                 ctypes.c_void_p(ga.data_ptr()) if ga is not None else None,
+                                 ctypes.c_void_p(da.data_ptr()), float(gap_tau)),
+            ctx.ptr, "bks_backward")
+    return da
+
+
+def _autograd_function():
+    torch = _torch()
+
+    class RandSVD(torch.autograd.Function):
+        """(Sigma_k, A_k = Z Z^T A) of a randomized solve, differentiable in A.  The Ritz
+        triplets are the saved forward state; the backward is one bks_backward call (not
+        an unrolling of the iterations)."""
+
+        @staticmethod
+        def forward(ctx, a, k, q, seed, pi, method, precision, gap_tau):
+            u, s, v = ritz_triplets(a.detach(), k, q, seed=seed, pi=pi, method=method, precision=precision)
+            ctx.save_for_backward(u, s, v)
+            ctx.k, ctx.gap_tau, ctx.in_dtype = k, gap_tau, a.dtype
+            return s[:k].clone(), low_rank(u, s, v, k)
+
+        @staticmethod
+        def backward(ctx, g_sigma, g_ak):
+            u, s, v = ctx.saved_tensors
+            da = backward(u, s, v, ctx.k, g_sigma, g_ak, ctx.gap_tau)
+            return da.to(ctx.in_dtype), None, None, None, None, None, None, None
+
+    return RandSVD
+
+
+_RANDSVD = None
+
+
+def rand_svd(a, k, q, seed=0, pi=None, method="bki", precision="auto", gap_tau=0.0):
+    """Differentiable (Sigma_k, A_k) of Block Krylov (method "bki") or Simultaneous
+    Iteration ("si") on a dense CUDA matrix."""
+    global _RANDSVD
+    if _RANDSVD is None:
+        _RANDSVD = _autograd_function()
+    return _RANDSVD.apply(a, k, q, seed, pi, method, precision, gap_tau)
+
+
+# ---------------------------------------------------------------------- batches
+def block_krylov_batched(mats, k, q, seeds=None, pis=None, want_v=False, precision="auto", stats=False, **kw):
+    """Algorithm 2 on a list of independent matrices (dense CUDA tensors or CsrMatrix) in
+    one call (bks_block_krylov_batched).  Returns a list of (Z_i, sigma_i[, V_i]) and,
+    with stats, the summed bks_stats and the per-matrix statuses."""
+    torch = _torch()
+    b = len(mats)
+    if b == 0:
+        return []
+    arr = (BksMatrix * b)()
+    outs, zp, sp, vp, pp = [], (ctypes.c_void_p * b)(), (ctypes.c_void_p * b)(), (ctypes.c_void_p * b)(), \
+        (ctypes.c_void_p * b)()
+    dev = None
+    for i, a in enumerate(mats):
+        m, dv, odt = _as_bks(a, precision)
+        dev = dv if dev is None else dev
+        arr[i] = m
+        z = torch.empty((m.n, k), dtype=odt, device=dv)
+        s = torch.empty((k,), dtype=odt, device=dv)
+        v = torch.empty((m.d, k), dtype=odt, device=dv) if want_v else None
+        zp[i], sp[i] = z.data_ptr(), s.data_ptr()
+        if v is not None:
+            vp[i] = v.data_ptr()
+        if pis is not None and pis[i] is not None:
+            p = pis[i]
+            if p.shape != (m.d, k) or p.dtype != odt or not p.is_contiguous():
+                raise ValueError(f"pis[{i}] must be a contiguous {m.d}x{k} {odt} tensor")
+            pp[i] = p.data_ptr()
+        outs.append((z, s, v) if want_v else (z, s))
+    ctx = context(dev)
+    seeds_arr = (ctypes.c_uint64 * b)(*[int(x) & (2**64 - 1) for x in (seeds if seeds is not None else range(b))])
+    statuses = (ctypes.c_int32 * b)()
+    opts = _opts(precision=precision, **kw)
+    st = BksStats()
+    status = ctx.lib.bks_block_krylov_batched(ctx.ptr, b, arr, int(k), int(q), ctypes.cast(seeds_arr, ctypes.c_void_p),
+                                              ctypes.cast(pp, ctypes.c_void_p) if pis is not None else None,
+                                              ctypes.cast(zp, ctypes.c_void_p), ctypes.cast(sp, ctypes.c_void_p),
+                                              ctypes.cast(vp, ctypes.c_void_p) if want_v else None,
+                                              ctypes.byref(opts), ctypes.byref(st),
+                                              ctypes.cast(statuses, ctypes.c_void_p))
+    B.check(status, ctx.ptr, "bks_block_krylov_batched")
+    if stats:
+        return outs, st.as_dict(), list(statuses)
+    return outs

@@ -15,13 +15,26 @@
 
 #include "../../include/bks.h"
 #include "common.cuh"
+#include "ctx.cuh"
 
 
 using namespace bks;
 
+// A solve whose status has been queued for copy-back but not yet read (batched calls).
+struct PendingSolve {
+    bool active = false;
+    int q_eff = 0, w = 0;
+    bool deflated = false, basis_only = false;
+    int launches = 0, product_launches = 0;
+    double product_bytes = 0, product_flops = 0;
+};
+
 struct bks_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    bool own_stream = false;            // sub-contexts of batched calls own their stream
+    std::vector<bks_ctx*> subs;         // batched calls: one sub-context per stream
+    PendingSolve pending;
     int num_sms = 148;
     void* ws = nullptr;
     size_t ws_bytes = 0;
@@ -38,6 +51,7 @@ struct bks_ctx {
 namespace {
 
 constexpr int BKS_VERSION = 100;
+constexpr int BKS_BATCH_STREAMS = 8;   // solves of a batch in flight at once
 
 struct Arena {
     size_t off = 0;
@@ -295,7 +309,7 @@ int64_t max_partials(int64_t n, int64_t d, int k, int w, int sms) {
     return p;
 }
 
-Plan make_plan(const bks_matrix* A, int k, int q_eff, int w, size_t tb, int sms) {
+Plan make_plan(const bks_matrix* A, int k, int q_eff, int w, size_t tb, int sms, int kout) {
     const int64_t n = A->n, d = A->d;
     Plan p{};
     p.n = n; p.d = d; p.k = k; p.q = q_eff; p.w = w;
@@ -332,7 +346,7 @@ Plan make_plan(const bks_matrix* A, int k, int q_eff, int w, size_t tb, int sms)
     p.nrm = a.take(size_t(w) * tb);
     p.Vt = a.take(size_t(w) * w * tb);
     p.order = a.take(size_t(w) * sizeof(int));
-    p.Vk = a.take(size_t(k) * p.ldd * tb);
+    p.Vk = a.take(size_t(kout) * p.ldd * tb);
     const int64_t ldmax = p.ldn > p.ldd ? p.ldn : p.ldd;
     p.xh = a.take(size_t(k) * ldmax * 4);
     p.xl = a.take(size_t(k) * ldmax * 4);
@@ -395,9 +409,42 @@ struct Prof {
     }
 };
 
+// Wait for the queued solve of ctx, decode its status words and fill st.
+bks_status finish_solve(bks_ctx* ctx, bks_stats* st) {
+    PendingSolve ps = ctx->pending;
+    ctx->pending.active = false;
+    if (!ps.active) return BKS_OK;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "solve");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+    const int status = ctx->host_status[0];
+    if (st != nullptr) {
+        std::memset(st, 0, sizeof(*st));
+        st->q_eff = ps.q_eff;
+        st->width = ps.w;
+        st->jacobi_sweeps = ctx->host_status[1];
+        st->chol_shifts = ctx->host_status[2];
+        st->launches = ps.launches;
+        st->product_launches = ps.product_launches;
+        st->product_bytes = ps.product_bytes;
+        st->product_flops = ps.product_flops;
+    }
+    if (status & ST_TIMEOUT) return fail(ctx, BKS_ERR_TIMEOUT, "a bounded device-side wait gave up");
+    if (status & ST_BADINPUT) return fail(ctx, BKS_ERR_INVALID_ARG, "CSR structure check failed");
+    if (status & ST_NONFINITE) return fail(ctx, BKS_ERR_NONFINITE, "non-finite value in a Gram matrix or M");
+    if (status & ST_BREAKDOWN) return fail(ctx, BKS_ERR_BREAKDOWN, "Cholesky breakdown after shifting");
+    if (status & ST_NOT_CONVERGED) return fail(ctx, BKS_ERR_NOT_CONVERGED, "Jacobi sweep cap reached");
+    if (!ps.basis_only && ctx->host_status[1] < 0)
+        return fail(ctx, BKS_ERR_UNSUPPORTED, "Jacobi launch failed");
+    ctx->last_error.clear();
+    return ps.deflated ? BKS_WARN_DEFLATED : BKS_OK;
+}
+
 template <typename T>
 bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed, const void* pi,
-                 void* Zv, void* sigv, void* Vv, const bks_opts& o, bks_stats* st, bool krylov) {
+                 void* Zv, void* sigv, void* Vv, const bks_opts& o, bks_stats* st, bool krylov,
+                 bool triplets, bool defer) {
     const int64_t n = A->n, d = A->d;
     const int64_t mn = n < d ? n : d;
     int q_eff = q;
@@ -414,7 +461,8 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
             return fail(ctx, BKS_ERR_UNSUPPORTED,
                         "Krylov width " + std::to_string(w) + " exceeds the Jacobi solver's limit");
     }
-    Plan p = make_plan(A, k, q_eff, w, sizeof(T), ctx->num_sms);
+    const int kout = triplets ? w : k;   // Ritz triplets returned
+    Plan p = make_plan(A, k, q_eff, w, sizeof(T), ctx->num_sms, kout);
     bks_status s = ensure_ws(ctx, p.total);
     if (s != BKS_OK) return s;
     char* base = static_cast<char*>(ctx->ws);
@@ -564,41 +612,38 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
                    o.jacobi_max_sweeps > 0 ? o.jacobi_max_sweeps : 40, o.jacobi_tol, stat + 1);
         // a7: Z = Q Ubar_k (row-major n x k)
         GemmDesc gz{};
-        gz.M = k; gz.N = n; gz.K = w;
+        gz.M = kout; gz.N = n; gz.K = w;
         gz.X = Vt; gz.ldx = w; gz.Y = Qt; gz.ldy = p.ldn;
         gz.y_kmajor = false; gz.y_dtype = gm.y_dtype;
-        gz.out = Z; gz.ldo = k; gz.out_transposed = true; gz.alpha = 1.0; gz.beta = 0.0;
+        gz.out = Z; gz.ldo = kout; gz.out_transposed = true; gz.alpha = 1.0; gz.beta = 0.0;
         gemm_simt<T>(ex, gz, part, p.part_cap);
-        if (o.sign_fix) sign_fix<T>(ex, Z, n, k, k, Vt, w, w);
+        if (o.sign_fix) sign_fix<T>(ex, Z, n, kout, kout, Vt, w, w);
         // sigma_i = |B ubar_i| = |A^T z_i|; V_k = B Ubar_k Sigma^{-1}
         GemmDesc gv{};
-        gv.M = k; gv.N = d; gv.K = w;
+        gv.M = kout; gv.N = d; gv.K = w;
         gv.X = Vt; gv.ldx = w; gv.Y = Bt; gv.ldy = p.ldd;
         gv.y_kmajor = false; gv.y_dtype = gm.y_dtype;
         gv.out = Vk; gv.ldo = p.ldd; gv.alpha = 1.0; gv.beta = 0.0;
         gemm_simt<T>(ex, gv, part, p.part_cap);
-        row_norms<T>(ex, Vk, k, d, p.ldd, sigma, V != nullptr);
+        row_norms<T>(ex, Vk, kout, d, p.ldd, sigma, V != nullptr);
         if (V != nullptr)
-            transpose_in<T>(ex, Vk, sizeof(T) == 8 ? BKS_F64 : BKS_F32, k, d, p.ldd, V, k);
+            transpose_in<T>(ex, Vk, sizeof(T) == 8 ? BKS_F64 : BKS_F32, kout, d, p.ldd, V, kout);
     }
     prof.end(2, t_rr);
     prof.end(3, t_all);
 
     cudaError_t e = cudaMemcpyAsync(ctx->host_status, stat, 3 * sizeof(int), cudaMemcpyDeviceToHost,
                                     ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "solve");
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
-    const int status = ctx->host_status[0];
-    if (st != nullptr) {
-        std::memset(st, 0, sizeof(*st));
-        st->q_eff = q_eff;
-        st->width = w;
-        st->jacobi_sweeps = ctx->host_status[1];
-        st->chol_shifts = ctx->host_status[2];
-        st->launches = ex.launches;
-        st->product_launches = ex.product_launches;
+    PendingSolve ps;
+    ps.active = true;
+    ps.q_eff = q_eff;
+    ps.w = w;
+    ps.deflated = deflated;
+    ps.basis_only = o.basis_only != 0;
+    ps.launches = ex.launches;
+    ps.product_launches = ex.product_launches;
+    {
         const int nprod = 2 * q_eff + 2;   // q+1 products with A, q+1 with A^T (both methods)
         // A once per product (CSR: values + column indices, and the row offsets of A or of
         // A^T, averaged), the thin input read once and the thin output written once.
@@ -606,41 +651,39 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
                                   ? double(A->nnz) * 8.0 + double(n + d + 2) * 4.0
                                   : double(n) * double(A->ld) * double(dtype_bytes(A->dtype));
         const double nnz_like = A->kind == BKS_CSR ? double(A->nnz) : double(n) * double(d);
-        st->product_bytes = nprod * (abytes + double(k) * (n + d) * sizeof(T));
-        st->product_flops = nprod * 2.0 * k * nnz_like;
+        ps.product_bytes = nprod * (abytes + double(k) * (n + d) * sizeof(T));
+        ps.product_flops = nprod * 2.0 * k * nnz_like;
         if (refine) {   // the last A^T product runs at width w (groups of 128 columns)
             const double groups = double((w + 127) / 128);
-            st->product_bytes += groups * abytes + double(w - k) * (n + d) * sizeof(T);
-            st->product_flops += 2.0 * (w - k) * nnz_like;
-        }
-        if (o.profile) {
-            st->ms_product = prof.total(0);
-            st->ms_orth = prof.total(1);
-            st->ms_rr = prof.total(2);
-            st->ms_total = prof.total(3);
-            float kms = 0.f;
-            for (int i = 0; i + 1 < ctx->klog.n; i += 2) {
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, ctx->klog.ev[i], ctx->klog.ev[i + 1]);
-                kms += ms;
-            }
-            st->ms_product_kernel = kms;
-            st->product_kernel_launches = ctx->klog.n / 2;
+            ps.product_bytes += groups * abytes + double(w - k) * (n + d) * sizeof(T);
+            ps.product_flops += 2.0 * (w - k) * nnz_like;
         }
     }
-    if (status & ST_BADINPUT) return fail(ctx, BKS_ERR_INVALID_ARG, "CSR structure check failed");
-    if (status & ST_NONFINITE) return fail(ctx, BKS_ERR_NONFINITE, "non-finite value in a Gram matrix or M");
-    if (status & ST_BREAKDOWN) return fail(ctx, BKS_ERR_BREAKDOWN, "Cholesky breakdown after shifting");
-    if (status & ST_NOT_CONVERGED) return fail(ctx, BKS_ERR_NOT_CONVERGED, "Jacobi sweep cap reached");
-    if (!o.basis_only && ctx->host_status[1] < 0)
-        return fail(ctx, BKS_ERR_UNSUPPORTED, "Jacobi launch failed");
-    ctx->last_error.clear();
-    return deflated ? BKS_WARN_DEFLATED : BKS_OK;
+    if (defer) {   // the caller reads the status later (finish_solve)
+        ctx->pending = ps;
+        return BKS_OK;
+    }
+    const bks_status result = finish_solve(ctx, st);
+    if (st != nullptr && o.profile) {
+        st->ms_product = prof.total(0);
+        st->ms_orth = prof.total(1);
+        st->ms_rr = prof.total(2);
+        st->ms_total = prof.total(3);
+        float kms = 0.f;
+        for (int i = 0; i + 1 < ctx->klog.n; i += 2) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ctx->klog.ev[i], ctx->klog.ev[i + 1]);
+            kms += ms;
+        }
+        st->ms_product_kernel = kms;
+        st->product_kernel_launches = ctx->klog.n / 2;
+    }
+    return result;
 }
 
 bks_status solve_entry(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
                        const void* pi, void* Z, void* sigma, void* V, const bks_opts* opts,
-                       bks_stats* st, bool krylov) {
+                       bks_stats* st, bool krylov, bool triplets = false, bool defer = false) {
     if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
     bks_status s = check_matrix(ctx, A);
     if (s != BKS_OK) return s;
@@ -662,12 +705,35 @@ bks_status solve_entry(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t
     DeviceGuard g(ctx->device);
     if (A->kind == BKS_CSR && prec != BKS_PREC_F32)
         return fail(ctx, BKS_ERR_UNSUPPORTED, "a CSR matrix is solved on the FP32 path");
-    if (prec == BKS_PREC_F64) return solve<double>(ctx, A, k, q, seed, pi, Z, sigma, V, o, st, krylov);
+    if (triplets && o.basis_only)
+        return fail(ctx, BKS_ERR_INVALID_ARG, "Ritz triplets need the Rayleigh-Ritz step (basis_only = 0)");
+    if (defer) o.profile = 0;
+    if (prec == BKS_PREC_F64)
+        return solve<double>(ctx, A, k, q, seed, pi, Z, sigma, V, o, st, krylov, triplets, defer);
     // BF16 and F32 both run the FP32 pipeline (Krylov blocks, Z, sigma in FP32)
-    return solve<float>(ctx, A, k, q, seed, pi, Z, sigma, V, o, st, krylov);
+    return solve<float>(ctx, A, k, q, seed, pi, Z, sigma, V, o, st, krylov, triplets, defer);
 }
 
 }  // namespace
+
+namespace bks {
+
+int ctx_num_sms(const bks_ctx* ctx) { return ctx->num_sms; }
+
+bks_status ctx_workspace(bks_ctx* ctx, size_t bytes, CtxInfo* info) {
+    DeviceGuard g(ctx->device);
+    const bks_status s = ensure_ws(ctx, bytes);
+    if (s != BKS_OK) return s;
+    info->ws = ctx->ws;
+    info->stream = ctx->stream;
+    info->num_sms = ctx->num_sms;
+    info->device = ctx->device;
+    return BKS_OK;
+}
+
+bks_status ctx_fail(bks_ctx* ctx, bks_status s, const char* msg) { return fail(ctx, s, msg); }
+
+}  // namespace bks
 
 // ====================================================================== C-ABI
 
@@ -729,7 +795,10 @@ bks_status bks_create(bks_ctx** out, int device) {
 bks_status bks_destroy(bks_ctx* ctx) {
     if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
+    for (bks_ctx* sub : ctx->subs) bks_destroy(sub);
+    ctx->subs.clear();
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     if (ctx->ws_owned && ctx->ws) cudaFree(ctx->ws);
     for (auto e : ctx->events) cudaEventDestroy(e);
     if (ctx->host_status) cudaFreeHost(ctx->host_status);
@@ -779,7 +848,7 @@ bks_status bks_workspace_size(const bks_matrix* A, int k, int q, int method, con
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaGetLastError();
-    *bytes = make_plan(A, k, q_eff, w, tb, sms).total;
+    *bytes = make_plan(A, k, q_eff, w, tb, sms, w).total;   // enough for the Ritz triplets too
     return BKS_OK;
 }
 
@@ -793,6 +862,94 @@ bks_status bks_simul_iter(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint6
                           const void* pi, void* Z, void* sigma, void* V, const bks_opts* opts,
                           bks_stats* stats) {
     return solve_entry(ctx, A, k, q, seed, pi, Z, sigma, V, opts, stats, false);
+}
+
+bks_status bks_block_krylov_batched(bks_ctx* ctx, int batch, const bks_matrix* As, int k, int q,
+                                    const uint64_t* seeds, const void* const* pis, void* const* Zs,
+                                    void* const* sigmas, void* const* Vs, const bks_opts* opts,
+                                    bks_stats* stats, bks_status* statuses) {
+    if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
+    if (batch < 0 || (batch > 0 && (As == nullptr || Zs == nullptr || sigmas == nullptr)))
+        return fail(ctx, BKS_ERR_INVALID_ARG, "bad bks_block_krylov_batched arguments");
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (batch == 0) return BKS_OK;
+    DeviceGuard g(ctx->device);
+    const int S = batch < BKS_BATCH_STREAMS ? batch : BKS_BATCH_STREAMS;
+    while (int(ctx->subs.size()) < S) {
+        bks_ctx* sub = nullptr;
+        bks_status cs = bks_create(&sub, ctx->device);
+        if (cs != BKS_OK) return fail(ctx, cs, "could not create a stream context for the batch");
+        if (cudaStreamCreateWithFlags(&sub->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            bks_destroy(sub);
+            return fail(ctx, BKS_ERR_CUDA, "could not create a stream for the batch");
+        }
+        sub->own_stream = true;
+        ctx->subs.push_back(sub);
+    }
+    {   // size every stream's workspace for the largest matrix once (no reallocation mid-batch)
+        size_t need = 0;
+        for (int i = 0; i < batch; ++i) {
+            size_t b = 0;
+            if (bks_workspace_size(&As[i], k, q, 0, opts, &b) == BKS_OK && b > need) need = b;
+        }
+        for (int j = 0; j < S; ++j)
+            if (need > 0 && ensure_ws(ctx->subs[j], need) != BKS_OK)
+                return fail(ctx, BKS_ERR_NOMEM, "could not allocate the batch workspaces");
+    }
+    // the batch starts after the work already queued on the caller's stream
+    cudaEvent_t start;
+    cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
+    cudaEventRecord(start, ctx->stream);
+    for (int j = 0; j < S; ++j) cudaStreamWaitEvent(ctx->subs[j]->stream, start, 0);
+    std::vector<int> owner(S, -1);
+    bks_status worst = BKS_OK;
+    auto note = [&](int i, bks_status st_i, const bks_stats& one) {
+        if (statuses) statuses[i] = st_i;
+        if (st_i != BKS_OK && (worst == BKS_OK || (worst == BKS_WARN_DEFLATED && st_i != BKS_WARN_DEFLATED)))
+            worst = st_i;
+        if (stats) {
+            stats->q_eff = one.q_eff;
+            stats->width = one.width;
+            stats->jacobi_sweeps = one.jacobi_sweeps > stats->jacobi_sweeps ? one.jacobi_sweeps : stats->jacobi_sweeps;
+            stats->chol_shifts += one.chol_shifts;
+            stats->launches += one.launches;
+            stats->product_launches += one.product_launches;
+            stats->product_bytes += one.product_bytes;
+            stats->product_flops += one.product_flops;
+        }
+    };
+    for (int i = 0; i < batch; ++i) {
+        bks_ctx* sub = ctx->subs[i % S];
+        bks_stats one{};
+        if (owner[i % S] >= 0) note(owner[i % S], finish_solve(sub, &one), one);
+        owner[i % S] = -1;
+        one = bks_stats{};
+        const bks_status st_i = solve_entry(sub, &As[i], k, q, seeds ? seeds[i] : uint64_t(i),
+                                            pis ? pis[i] : nullptr, Zs[i], sigmas[i], Vs ? Vs[i] : nullptr, opts,
+                                            nullptr, true, false, true);
+        if (sub->pending.active) owner[i % S] = i;
+        else note(i, st_i, one);
+    }
+    for (int j = 0; j < S; ++j) {
+        bks_stats one{};
+        if (owner[j] >= 0) note(owner[j], finish_solve(ctx->subs[j], &one), one);
+        // later work on the caller's stream is ordered after the batch
+        cudaEventRecord(start, ctx->subs[j]->stream);
+        cudaStreamWaitEvent(ctx->stream, start, 0);
+    }
+    cudaEventDestroy(start);
+    if (worst != BKS_OK && worst != BKS_WARN_DEFLATED)
+        return fail(ctx, worst, "at least one matrix of the batch failed (see statuses)");
+    ctx->last_error.clear();
+    return worst;
+}
+
+bks_status bks_ritz_triplets(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed, const void* pi,
+                             int method, void* U, void* sigma, void* V, const bks_opts* opts, bks_stats* stats) {
+    if (method != 0 && method != 1) return fail(ctx, BKS_ERR_INVALID_ARG, "method must be 0 (BKI) or 1 (SI)");
+    if (V == nullptr) return fail(ctx, BKS_ERR_INVALID_ARG, "V is required for the Ritz triplets");
+    return solve_entry(ctx, A, k, q, seed, pi, U, sigma, V, opts, stats, method == 0, true);
 }
 
 bks_status bks_gen_pi(bks_ctx* ctx, uint64_t seed, int64_t d, int k, int dtype, void* out) {
