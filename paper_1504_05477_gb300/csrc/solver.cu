@@ -659,10 +659,8 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
             ps.product_flops += 2.0 * (w - k) * nnz_like;
         }
     }
-    if (defer) {   // the caller reads the status later (finish_solve)
-        ctx->pending = ps;
-        return BKS_OK;
-    }
+    ctx->pending = ps;
+    if (defer) return BKS_OK;   // the caller reads the status later (finish_solve)
     const bks_status result = finish_solve(ctx, st);
     if (st != nullptr && o.profile) {
         st->ms_product = prof.total(0);
