@@ -813,9 +813,9 @@ bool orth_fused(Exec& ex, int64_t len, int64_t ld, const float* Qb, int m, float
         }
         configured_device[ti] = dev;
     }
-    // about 128 rows per CTA: a short block takes only a few SMs (other streams keep the rest)
+    // about 64 rows per CTA: a short block takes only a few SMs (other streams keep the rest)
     int G = ex.num_sms < of::MAXG ? ex.num_sms : of::MAXG;
-    const int64_t want = (len + 127) / 128;
+    const int64_t want = (len + 63) / 64;
     if (want < G) G = int(want < 1 ? 1 : want);
     if (per_sm[ti] < 1 || int64_t(G) * of::r4((m + c) * c) > ws.fpart_cap) return false;
     of::Args a;
