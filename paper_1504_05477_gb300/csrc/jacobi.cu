@@ -42,12 +42,32 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // Rotation coefficients; returns false when the pair is already orthogonal to tol.
+// With x = beta - alpha, y = 2 gamma and r = sqrt(x^2 + y^2), the smaller root of
+// t^2 + 2 (x / y) t - 1 = 0 is t = sign(x) y / (|x| + r) (no cancellation; x = 0 gives
+// t = sign(y)), then
+// c = 1 / sqrt(1 + t^2), s = c t.  The threshold |gamma| > tol sqrt(alpha beta) is
+// tested squared.
 template <typename T>
 __device__ __forceinline__ bool rot_coeffs(T alpha, T beta, T gamma, T tol, T& c, T& s, T& t) {
-    if (gamma == T(0) || !(fabs(gamma) > tol * sqrt(alpha * beta))) return false;
-    const T zeta = (beta - alpha) / (T(2) * gamma);
-    t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-    c = T(1) / sqrt(T(1) + t * t);
+    if (!(gamma * gamma > tol * tol * (alpha * beta)) || gamma == T(0)) return false;
+    const T x = beta - alpha, y = T(2) * gamma;
+    const T r = sqrt(fma(x, x, y * y));
+    t = (x >= T(0) ? y : -y) / (fabs(x) + r);   // sign(x) y / (|x| + r)
+    c = T(1) / sqrt(fma(t, t, T(1)));
+    s = c * t;
+    return true;
+}
+// FP32: the same formulas on the special-function unit (rsqrt and reciprocal
+// approximations, within a few ulp: the rotation stays orthogonal to rounding level).
+template <>
+__device__ __forceinline__ bool rot_coeffs<float>(float alpha, float beta, float gamma, float tol, float& c,
+                                                  float& s, float& t) {
+    if (!(gamma * gamma > tol * tol * (alpha * beta)) || gamma == 0.f) return false;
+    const float x = beta - alpha, y = 2.f * gamma;
+    const float r2 = fmaf(x, x, y * y);
+    const float r = r2 * rsqrtf(r2);
+    t = (x >= 0.f ? y : -y) * __frcp_rn(fabsf(x) + r);   // sign(x) y / (|x| + r)
+    c = rsqrtf(fmaf(t, t, 1.f));
     s = c * t;
     return true;
 }
