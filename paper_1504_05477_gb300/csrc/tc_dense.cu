@@ -12,8 +12,8 @@
 // One persistent CTA per SM.  The (tile, 32-deep chunk) units of the whole product are
 // dealt out in equal contiguous ranges (stream-K); a tile cut between CTAs is summed
 // by a fix-up kernel in CTA order, so results are deterministic.
-//   warp 0      TMA: raw A tiles -> 6-deep ring
-//   warp 1      TMA: [hi(X) | lo(X)] tiles -> 2-deep operand ring
+//   warp 0      TMA: raw A tiles -> 4-deep ring
+//   warp 1      TMA: [hi(X) | lo(X)] tiles -> their own ring, 2 to 6 deep by width
 //   warp 2      tcgen05.mma issue (one thread); owns the TMEM allocation
 //   warps 3-6   converters: raw A -> hi(A), lo(A) in the UMMA K-major 128B-swizzled
 //               layout (for A^T X this is also the transpose)
@@ -26,8 +26,12 @@ namespace bks {
 namespace tc {
 
 constexpr int KC = 32;             // contraction depth per chunk (128 bytes of FP32)
-constexpr int RA = 6;              // raw A ring depth
-constexpr int OP = 2;              // operand ring depth
+constexpr int RA = 4;              // raw A ring depth
+constexpr int OP = 2;              // converted A (hi / lo) ring depth
+// ring depth of the [hi(X) | lo(X)] tiles, streamed from L2 once per chunk: as deep as
+// shared memory allows, so their L2 round trips overlap
+__host__ __device__ constexpr int x_ring(int cp) { return cp <= 32 ? 6 : cp <= 64 ? 4 : cp <= 96 ? 3 : 2; }
+constexpr int XR_MAX = 6;
 constexpr int NWARP = 11;
 constexpr int NTHREADS = NWARP * 32;
 constexpr uint32_t TILE_BYTES = BM * KC * 4;   // 16 KB
@@ -51,7 +55,8 @@ __device__ __forceinline__ float tf32_hi(float v) {
 
 struct Smem {
     uint64_t raw_full[RA], raw_empty[RA];
-    uint64_t b_full[OP], op_empty[OP], conv_full[OP];
+    uint64_t op_empty[OP], conv_full[OP];
+    uint64_t x_full[XR_MAX], x_empty[XR_MAX];
     uint64_t acc_full[2], acc_empty[2];
     uint64_t drain;
     uint32_t tmem_base;
@@ -70,8 +75,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     unsigned char* raw = base;                                   // RA x 16 KB
     unsigned char* hi = raw + RA * TILE_BYTES;                   // OP x 16 KB
     unsigned char* lo = hi + OP * TILE_BYTES;                    // OP x 16 KB
-    unsigned char* bop = lo + OP * TILE_BYTES;                   // OP x b_bytes
-    Smem* sm = reinterpret_cast<Smem*>(bop + OP * b_bytes);
+    constexpr int XR = x_ring(CP);
+    unsigned char* bop = lo + OP * TILE_BYTES;                   // XR x b_bytes
+    Smem* sm = reinterpret_cast<Smem*>(bop + XR * b_bytes);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int G = gridDim.x, cta = blockIdx.x;
@@ -83,9 +89,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (tid == 0) {
         for (int i = 0; i < RA; ++i) { mbar_init(&sm->raw_full[i], 1); mbar_init(&sm->raw_empty[i], 4); }
         for (int i = 0; i < OP; ++i) {
-            mbar_init(&sm->b_full[i], 1);
             mbar_init(&sm->op_empty[i], 1);
             mbar_init(&sm->conv_full[i], 4);
+        }
+        for (int i = 0; i < XR; ++i) {
+            mbar_init(&sm->x_full[i], 1);
+            mbar_init(&sm->x_empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) { mbar_init(&sm->acc_full[i], 1); mbar_init(&sm->acc_empty[i], 4); }
         mbar_init(&sm->drain, 1);
@@ -127,20 +136,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else if (warp == 1) {
         // ---------------------------------------------------------------- X producer
         if (lane == 0) {
-            int last[OP];
-            for (int o = 0; o < OP; ++o) last[o] = -1;
+            int last[XR_MAX];
+            for (int o = 0; o < XR_MAX; ++o) last[o] = -1;
             int64_t i = 0;
             for (int64_t u = ustart; u < uend; ++u, ++i) {
-                const int o = int(i % OP);
-                if (!wait_bar(&sm->op_empty[o], uint32_t(((i / OP) & 1) ^ 1), abort_flag, p.status)) break;
+                const int o = int(i % XR);
+                if (!wait_bar(&sm->x_empty[o], uint32_t(((i / XR) & 1) ^ 1), abort_flag, p.status)) break;
                 const int64_t kc = u % p.cpt;
-                mbar_expect_tx(&sm->b_full[o], b_bytes);
+                mbar_expect_tx(&sm->x_full[o], b_bytes);
                 unsigned char* dst = bop + o * b_bytes;
-                tma_load_2d(dst, &tmXh, int(kc * KC), 0, &sm->b_full[o]);
-                tma_load_2d(dst + CP * 128, &tmXl, int(kc * KC), 0, &sm->b_full[o]);
-                last[o] = int((i / OP) & 1);
+                tma_load_2d(dst, &tmXh, int(kc * KC), 0, &sm->x_full[o]);
+                tma_load_2d(dst + CP * 128, &tmXl, int(kc * KC), 0, &sm->x_full[o]);
+                last[o] = int((i / XR) & 1);
             }
-            for (int o = 0; o < OP; ++o) drain_bar(&sm->b_full[o], last[o]);
+            for (int o = 0; o < XR; ++o) drain_bar(&sm->x_full[o], last[o]);
         }
     } else if (warp == 2) {
         // ---------------------------------------------------------------- MMA issuer
@@ -158,15 +167,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     first = true;
                 }
                 (void)t;
-                const int o = int(i % OP);
+                const int o = int(i % OP), xs = int(i % XR);
                 const uint32_t par = uint32_t((i / OP) & 1);
                 if (!wait_bar(&sm->conv_full[o], par, abort_flag, p.status)) break;
-                if (!wait_bar(&sm->b_full[o], par, abort_flag, p.status)) break;
+                if (!wait_bar(&sm->x_full[xs], uint32_t((i / XR) & 1), abort_flag, p.status)) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + uint32_t((sub & 1) * 256);
                 const uint64_t dh = desc_sw128(smem_u32(hi + o * TILE_BYTES));
                 const uint64_t dl = desc_sw128(smem_u32(lo + o * TILE_BYTES));
-                const uint64_t db = desc_sw128(smem_u32(bop + o * b_bytes));
+                const uint64_t db = desc_sw128(smem_u32(bop + xs * b_bytes));
 #pragma unroll
                 for (int kk = 0; kk < KC / 8; ++kk) {   // K = 8 per tf32 MMA = 32 bytes
                     const uint64_t adv = uint64_t(kk * 2);
@@ -175,6 +184,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 first = false;
                 umma_commit(&sm->op_empty[o]);
+                umma_commit(&sm->x_empty[xs]);
                 if (u + 1 == uend || window_start(u + 1, ustart, p.cpt, FLUSH))
                     umma_commit(&sm->acc_full[sub & 1]);
             }
@@ -410,7 +420,7 @@ int64_t partial_floats(int64_t rows_out, int64_t len, int kc, int cp, int num_sm
 }
 
 size_t smem_bytes(int cp) {
-    return size_t(RA) * TILE_BYTES + size_t(2 * OP) * TILE_BYTES + size_t(OP) * 2 * cp * 128 +
+    return size_t(RA) * TILE_BYTES + size_t(2 * OP) * TILE_BYTES + size_t(x_ring(cp)) * 2 * cp * 128 +
            sizeof(Smem) + 1024;
 }
 
