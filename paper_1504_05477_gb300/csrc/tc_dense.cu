@@ -12,8 +12,8 @@
 // One persistent CTA per SM.  The (tile, 32-deep chunk) units of the whole product are
 // dealt out in equal contiguous ranges (stream-K); a tile cut between CTAs is summed
 // by a fix-up kernel in CTA order, so results are deterministic.
-//   warp 0      TMA: raw A tiles -> 4-deep ring
-//   warp 1      TMA: [hi(X) | lo(X)] tiles -> their own ring, 2 to 6 deep by width
+//   warp 0      TMA: raw A tiles -> 6-deep ring
+//   warp 1      TMA: [hi(X) | lo(X)] tiles -> their own ring (2 or 4 deep)
 //   warp 2      tcgen05.mma issue (one thread); owns the TMEM allocation
 //   warps 3-6   converters: raw A -> hi(A), lo(A) in the UMMA K-major 128B-swizzled
 //               layout (for A^T X this is also the transpose)
@@ -26,11 +26,11 @@ namespace bks {
 namespace tc {
 
 constexpr int KC = 32;             // contraction depth per chunk (128 bytes of FP32)
-constexpr int RA = 4;              // raw A ring depth
+constexpr int RA = 6;              // raw A ring depth
 constexpr int OP = 2;              // converted A (hi / lo) ring depth
 // ring depth of the [hi(X) | lo(X)] tiles, streamed from L2 once per chunk: as deep as
 // shared memory allows, so their L2 round trips overlap
-__host__ __device__ constexpr int x_ring(int cp) { return cp <= 32 ? 6 : cp <= 64 ? 4 : cp <= 96 ? 3 : 2; }
+__host__ __device__ constexpr int x_ring(int cp) { return cp <= 32 ? 4 : 2; }
 constexpr int XR_MAX = 6;
 constexpr int NWARP = 11;
 constexpr int NTHREADS = NWARP * 32;
@@ -270,15 +270,28 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 tc_fence_after();
                 const uint32_t acc = tmem + uint32_t((sub & 1) * 256) + (uint32_t(grp * 32) << 16);
+                if constexpr (CP <= 64) {   // hi.hi and hi.lo halves, one wait per 32 columns
 #pragma unroll
-                for (int j0 = 0; j0 < CP; j0 += 32) {
-                    float h[32];
-                    tmem_ld32(acc + uint32_t(j0), h);
+                    for (int j0 = 0; j0 < CP; j0 += 32) {
+                        uint32_t hh[32], hl[32];
+                        tmem_ld32_async(acc + uint32_t(j0), hh);
+                        tmem_ld32_async(acc + uint32_t(CP + j0), hl);
+                        tmem_wait();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) run[j0 + j] += h[j];
-                    tmem_ld32(acc + uint32_t(CP + j0), h);
+                        for (int j = 0; j < 32; ++j)
+                            run[j0 + j] += __uint_as_float(hh[j]) + __uint_as_float(hl[j]);
+                    }
+                } else {   // wide tiles: the registers hold one load at a time
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) run[j0 + j] += h[j];
+                    for (int j0 = 0; j0 < CP; j0 += 32) {
+                        float h[32];
+                        tmem_ld32(acc + uint32_t(j0), h);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) run[j0 + j] += h[j];
+                        tmem_ld32(acc + uint32_t(CP + j0), h);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) run[j0 + j] += h[j];
+                    }
                 }
                 tc_fence_before();
                 __syncwarp();
