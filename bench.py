@@ -2,6 +2,12 @@
 dense FP32 20000 x 8000 workload (rank-200 planted exp(-i/40) spectrum + 1e-3 Gaussian
 noise, k = 50, q = 8, Krylov width 450), one solve per GPU per step.
 
+--workload picks one of the other workloads instead (their lines are reported, not the
+headline): sparse (centred CSR 200000 x 60000, 1e7 nnz, k = 20, q = 10), bf16 (dense
+BF16 65536 x 16384, k = 100, q = 6, BF16 products + FP32 refinement) or batched (256
+dense FP32 matrices m ~ U[256, 4096] x n ~ U[128, 2048], k = 16, q = 4, one
+bks_block_krylov_batched call per step; value = ms per solve).
+
 Prints ONE JSON line (rank 0).  `value` is the whole-job time per solve: the
 max-over-ranks wall time of the K timed steps divided by the number of solves all
 ranks finished (N per step).  A is 640 MB, larger than the 129 MB L2, so no flush is
@@ -35,6 +41,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--method", default="bki", choices=["bki", "si"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default="dense", choices=["dense", "sparse", "bf16", "batched"])
     return p.parse_args()
 
 
@@ -98,18 +105,25 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "tc_product_kernel_dense_20000x8000_k50.md")
-KERNEL_SOURCE = os.path.join(ROOT, "paper_1504_05477_gb300", "csrc", "tc_dense.cu")
+# committed ncu summary and kernel source of the dominant kernel of each workload
+TRAFFIC = {
+    "dense": ("tc_product_kernel_dense_20000x8000_k50.md", "tc_dense.cu"),
+    "sparse": ("spmm_seg_kernel_csr_200000x60000_k20.md", "csr.cu"),
+    "bf16": ("bf16_product_kernel_dense_65536x16384.md", "tc_bf16.cu"),
+}
 
 
-def measured_traffic():
+def measured_traffic(workload="dense"):
     """DRAM bytes (read + write) per launch of the product kernel from the committed ncu
     summary, or None when the kernel source changed since that capture."""
     import hashlib
+    if workload not in TRAFFIC:
+        return None
+    summary, source = TRAFFIC[workload]
     try:
-        with open(TRAFFIC_SUMMARY) as f:
+        with open(os.path.join(ROOT, "profiles", summary)) as f:
             text = f.read()
-        with open(KERNEL_SOURCE, "rb") as f:
+        with open(os.path.join(ROOT, "paper_1504_05477_gb300", "csrc", source), "rb") as f:
             digest = hashlib.sha256(f.read()).hexdigest()
     except OSError:
         return None
@@ -177,12 +191,141 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+class Setup:
+    """One workload: device input, the timed call and how to report it."""
+
+    def __init__(self, workload, rank, dev, method):
+        import numpy as np
+        import torch
+
+        import paper_1504_05477_gb300 as bk
+        import synth
+        self.name = workload
+        self.solve = bk.block_krylov if method == "bki" else bk.simul_iter
+        self.method = method
+        self.batch = None
+        self.cpu = None
+        if workload == "dense":
+            self.k, self.q = K_RANK, Q_ITERS
+            self.host = make_input(rank)
+            self.a = torch.from_numpy(self.host).to(dev)
+            self.desc = WORKLOAD
+            self.shape = {"n": N_ROWS, "d": N_COLS}
+            self.l2 = "A is 640 MB > 129 MB L2: inputs larger than L2, no flush"
+            self.dtype = "f32"
+            self.kernel = "tc_product_kernel (tcgen05 3xTF32, TMA, TMEM)"
+            self.cpu = lambda: cpu_baseline(self.host)
+        elif workload == "sparse":
+            self.k, self.q = 20, 10
+            rp, ci, cv, d = synth.zipf_idf_csr(seed=1003 + 100 * rank)
+            mu = synth.column_means(rp, ci, cv, 200000, d)
+            self.host = (rp, ci, cv, mu)
+            t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+            self.csr_args = lambda: (t(rp), t(ci), t(cv), (200000, d))
+            self.a = bk.CsrMatrix(*self.csr_args(), col_mean=t(mu))   # setup (CSR of A^T) untimed
+            self.desc = ("CSR 200000x60000, 50 Zipf(1.1) columns per row, lognormal x idf values, "
+                         "centred implicitly (A - 1 mu^T), k=20, q=10 (width 220)")
+            self.shape = {"n": 200000, "d": d, "nnz": int(cv.size)}
+            self.l2 = "CSR (80 MB) + CSR of A^T (80 MB) > 129 MB L2: no flush"
+            self.dtype = "f32"
+            self.kernel = "spmm_seg_kernel (warp per 512-nnz segment, float4 gathers)"
+            self.cpu = lambda: sparse_cpu_baseline(rp, ci, cv, mu, d, self.k, self.q)
+        elif workload == "bf16":
+            self.k, self.q = 100, 6
+            self.a = synth.dense_bf16_planted_torch(m=65536, d=16384, seed=1004 + 100 * rank, device=dev)
+            self.host = None
+            self.desc = ("dense BF16 65536x16384, Hadamard-planted sigma_i = i^-1/2, k=100, q=6 (width 700), "
+                         "BF16 products with FP32 accumulation + one FP32-accurate refinement of B = A^T Q")
+            self.shape = {"n": 65536, "d": 16384}
+            self.l2 = "A is 2.1 GB > 129 MB L2: no flush"
+            self.dtype = "bf16 products, f32 blocks"
+            self.kernel = "bf16_product_kernel<128,1> (tcgen05 kind::f16, TMA, TMEM)"
+            self.solve_kw = {"precision": "bf16"}
+        else:   # batched
+            self.k, self.q = 16, 4
+            mats = synth.batched_planted(batch=256, k=16, seed=1005 + 100 * rank)
+            self.host = mats
+            self.batch = [torch.from_numpy(m).to(dev) for m in mats]
+            self.desc = ("256 dense FP32 matrices, m ~ U[256,4096] x n ~ U[128,2048], U diag(1/i) V^T + "
+                         "1e-3 N(0,1), k=16, q=4 (width 80), one bks_block_krylov_batched call")
+            self.shape = {"batch": 256, "total_bytes": int(sum(m.nbytes for m in mats))}
+            self.l2 = "2.4 GB of matrices > 129 MB L2: no flush"
+            self.dtype = "f32"
+            self.kernel = "whole batch (effective product bandwidth)"
+            self.bk = bk
+        self.solve_kw = getattr(self, "solve_kw", {})
+        self.units = 256 if workload == "batched" else 1
+
+    def run(self, seed, stats=False, profile=False):
+        if self.batch is not None:
+            out = self.bk.block_krylov_batched(self.batch, self.k, self.q,
+                                               seeds=[seed * 1000 + i for i in range(256)], stats=True)
+            return out[1] if stats else out[0]
+        r = self.solve(self.a, self.k, self.q, seed=seed, stats=stats, profile=profile, **self.solve_kw)
+        return r[2] if stats else r
+
+    def e2e(self, dev, seed):
+        """Host input -> device, solve, results -> host; returns (h2d, d2h) bytes."""
+        import numpy as np
+        import torch
+        if self.name == "dense":
+            ad = self.pinned.to(dev, non_blocking=True)
+            z, s = self.solve(ad, self.k, self.q, seed=seed)
+            zh, sh = z.cpu(), s.cpu()
+            return self.host.nbytes, zh.numel() * 4 + sh.numel() * 4
+        if self.name == "sparse":
+            import paper_1504_05477_gb300 as bk
+            parts = [x.to(dev, non_blocking=True) for x in self.pinned]
+            a = bk.CsrMatrix(parts[0], parts[1], parts[2], (200000, self.shape["d"]), col_mean=parts[3])
+            z, s = self.solve(a, self.k, self.q, seed=seed)
+            zh, sh = z.cpu(), s.cpu()
+            return sum(x.numel() * x.element_size() for x in self.pinned), zh.numel() * 4 + sh.numel() * 4
+        if self.name == "bf16":
+            ad = self.pinned.to(dev, non_blocking=True)
+            z, s = self.solve(ad, self.k, self.q, seed=seed, **self.solve_kw)
+            zh, sh = z.cpu(), s.cpu()
+            return self.pinned.numel() * 2, zh.numel() * 4 + sh.numel() * 4
+        mats = [m.to(dev, non_blocking=True) for m in self.pinned]
+        outs = self.bk.block_krylov_batched(mats, self.k, self.q, seeds=[seed * 1000 + i for i in range(256)])
+        d2h = 0
+        for z, s in outs:
+            d2h += z.cpu().numel() * 4 + s.cpu().numel() * 4
+        return sum(m.numel() * 4 for m in self.pinned), d2h
+
+    def pin(self):
+        import numpy as np
+        import torch
+        if self.name == "dense":
+            self.pinned = torch.from_numpy(self.host).pin_memory()
+        elif self.name == "sparse":
+            rp, ci, cv, mu = self.host
+            self.pinned = [torch.from_numpy(np.ascontiguousarray(x)).pin_memory() for x in (rp, ci, cv, mu)]
+        elif self.name == "bf16":
+            self.pinned = self.a.cpu().pin_memory()
+        else:
+            self.pinned = [torch.from_numpy(m).pin_memory() for m in self.host]
+
+
+def sparse_cpu_baseline(rp, ci, cv, mu, d, k, q):
+    """The FP64 oracle on the sparse workload (scipy CSR products), one full solve."""
+    import synth
+    from oracle import krylov
+    cores = len(os.sched_getaffinity(0))
+    op = krylov.centred_csr_op(rp, ci, cv, 200000, d, mu)
+    pi = synth.gaussian_pi(3, d, k)
+    t0 = time.perf_counter()
+    krylov.block_krylov(op, k, q, pi)
+    dt = time.perf_counter() - t0
+    return {"value": dt * 1e3, "unit": "ms per solve", "cores": cores, "kind": "oracle",
+            "sample": "1 full centred 200000x60000 k=20 q=10 Block Krylov solve, numpy/scipy FP64 "
+                      "(scipy sparse products single-threaded)"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
         return
-    import numpy as np
     import torch
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -193,11 +336,8 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    import paper_1504_05477_gb300 as bk
 
-    a_host = make_input(rank)
-    a = torch.from_numpy(a_host).to(dev)
-    solve = bk.block_krylov if args.method == "bki" else bk.simul_iter
+    w = Setup(args.workload, rank, dev, args.method)
 
     def barrier():
         if world > 1:
@@ -206,7 +346,7 @@ def main():
 
     # warm-up (also builds the workspace)
     for i in range(args.warmup):
-        solve(a, K_RANK, Q_ITERS, seed=2 + i)
+        w.run(2 + i)
     barrier()
 
     stream = torch.cuda.current_stream(dev)
@@ -216,7 +356,7 @@ def main():
     barrier()
     ev0.record(stream)
     for i in range(args.steps):
-        z, s = solve(a, K_RANK, Q_ITERS, seed=100 + i)
+        w.run(100 + i)
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
@@ -226,72 +366,82 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms_total = float(t.item())
     ms_per_step = ms_total / args.steps
-    value = ms_per_step / world
+    value = ms_per_step / (world * w.units)   # ms per solve over all ranks and matrices
 
-    # per-kernel-class event times of one profiled solve (same launch configuration)
-    _, _, st = solve(a, K_RANK, Q_ITERS, seed=7, stats=True, profile=True)
-    prof_runs = []
-    for i in range(3):
-        prof_runs.append(solve(a, K_RANK, Q_ITERS, seed=8 + i, stats=True, profile=True)[2])
-    ms_prod = statistics.median(r["ms_product"] for r in prof_runs)
-    nprod = 2 * Q_ITERS + 2
-    # algorithmic bytes of one product: A once, the thin operand and the result
-    bytes_per_product = st["product_bytes"] / nprod
     hbm_peak, _, peak_src = peaks()
-    klaunch = prof_runs[0]["product_kernel_launches"]
-    if klaunch > 0:   # the dominant kernel alone, timed by events around each launch
-        kernel = "tc_product_kernel (tcgen05 3xTF32, TMA, TMEM)"
-        ms_launch = statistics.median(r["ms_product_kernel"] / r["product_kernel_launches"]
-                                      for r in prof_runs)
-    else:             # CUDA-core fallback: the whole product phase
-        kernel = "gemm_tile_kernel (SIMT)"
-        ms_launch = ms_prod / nprod
-    achieved = bytes_per_product / (ms_launch * 1e-3) / 1e9
-    traffic = measured_traffic() if klaunch > 0 else None
+    nprod = 2 * w.q + 2
+    if w.batch is None:
+        # per-kernel-class event times of profiled solves (same launch configuration)
+        st = w.run(7, stats=True, profile=True)
+        prof_runs = [w.run(8 + i, stats=True, profile=True) for i in range(3)]
+        ms_prod = statistics.median(r["ms_product"] for r in prof_runs)
+        klaunch = prof_runs[0]["product_kernel_launches"]
+        # algorithmic bytes of one product: A once, the thin operand and the result (the
+        # BF16 refinement's wider product is left out: the kernel log times the others)
+        if w.name == "bf16":
+            bytes_per_product = 65536 * 16384 * 2 + w.k * (65536 + 16384) * 4
+        else:
+            bytes_per_product = st["product_bytes"] / nprod
+        if klaunch > 0:   # the dominant kernel alone, timed by events around each launch
+            kernel = w.kernel
+            ms_launch = statistics.median(r["ms_product_kernel"] / r["product_kernel_launches"]
+                                          for r in prof_runs)
+        else:             # CUDA-core fallback: the whole product phase
+            kernel = "gemm_tile_kernel (SIMT)"
+            ms_launch = ms_prod / nprod
+        achieved = bytes_per_product / (ms_launch * 1e-3) / 1e9
+        traffic = measured_traffic(w.name) if klaunch > 0 else None
+        phases = {"product": ms_prod, "orth": statistics.median(r["ms_orth"] for r in prof_runs),
+                  "rayleigh_ritz": statistics.median(r["ms_rr"] for r in prof_runs),
+                  "total_profiled": statistics.median(r["ms_total"] for r in prof_runs),
+                  "jacobi_sweeps": st["jacobi_sweeps"]}
+        launches = st["launches"]
+        width = st["width"]
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": peak_src,
+                "kernel": kernel, "ms_per_launch": ms_launch, "launches_per_step": klaunch,
+                "bytes_per_launch": bytes_per_product,
+                "ms_per_product_incl_split_and_fixup": ms_prod / nprod}
+    else:
+        st = w.run(7, stats=True)
+        achieved = st["product_bytes"] / (ms_per_step * 1e-3) / 1e9
+        phases = None
+        launches = st["launches"]
+        width = st["width"]
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+                "kernel": w.kernel, "ms_per_launch": ms_per_step, "launches_per_step": launches,
+                "bytes_per_launch": st["product_bytes"]}
 
-    # end to end through the public API: pinned host A -> device, solve, results -> host
-    a_pin = torch.from_numpy(a_host).pin_memory()
+    # end to end through the public API: pinned host input -> device, solve, results -> host
+    w.pin()
     barrier()
     t0 = time.perf_counter()
     e2e_steps = max(1, min(args.steps, 5))
     for i in range(e2e_steps):
-        ad = a_pin.to(dev, non_blocking=True)
-        z, s = solve(ad, K_RANK, Q_ITERS, seed=200 + i)
-        zh, sh = z.cpu(), s.cpu()
+        h2d, d2h = w.e2e(dev, 200 + i)
     barrier()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps / world
-    h2d = a_host.nbytes
-    d2h = zh.numel() * 4 + sh.numel() * 4
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps / (world * w.units)
 
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return
     cpu = None
-    if not args.no_cpu_baseline and world == 1:
-        cpu = cpu_baseline(a_host)
+    if not args.no_cpu_baseline and world == 1 and w.cpu is not None:
+        cpu = w.cpu()
+    config = {"workload": w.desc, "method": "block_krylov" if args.method == "bki" else "simul_iter",
+              "k": w.k, "q": w.q, "width": width, "parallelism": f"replicas x{world}", "l2": w.l2}
+    config.update(w.shape)
     line = {
         "metric": METRIC, "value": value, "unit": "ms per solve", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "method": "block_krylov" if args.method == "bki" else "simul_iter",
-                   "n": N_ROWS, "d": N_COLS, "k": K_RANK, "q": Q_ITERS, "width": st["width"],
-                   "parallelism": f"replicas x{world}",
-                   "l2": "A is 640 MB > 129 MB L2: inputs larger than L2, no flush"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": peak_src,
-                     "kernel": kernel, "ms_per_launch": ms_launch, "launches_per_step": klaunch,
-                     "bytes_per_launch": bytes_per_product,
-                     "ms_per_product_incl_split_and_fixup": ms_prod / nprod},
-        "phases_ms": {"product": ms_prod, "orth": statistics.median(r["ms_orth"] for r in prof_runs),
-                      "rayleigh_ritz": statistics.median(r["ms_rr"] for r in prof_runs),
-                      "total_profiled": statistics.median(r["ms_total"] for r in prof_runs),
-                      "jacobi_sweeps": st["jacobi_sweeps"]},
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": w.dtype,
+        "data": "synthetic", "config": config, "roofline": roof, "phases_ms": phases,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_ms, "unit": "ms per solve", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "gpu_launches": st["launches"] * args.steps,
+        "gpu_launches": launches * args.steps,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -103,8 +103,9 @@ typedef struct {
     float ms_total;             /* ... of the whole call */
     double product_bytes;       /* algorithmic bytes moved by the A / A^T products */
     double product_flops;       /* algorithmic flops of the A / A^T products */
-    float ms_product_kernel;    /* with opts.profile: summed event time of the tensor-core
-                                   product kernel launches alone */
+    float ms_product_kernel;    /* with opts.profile: summed event time of the launches of the
+                                   dominant product kernel alone (dense FP32: the tensor-core
+                                   kernel; BF16: its BF16-rounded products; CSR: the SpMM) */
     int32_t product_kernel_launches;
     int32_t reserved[6];
 } bks_stats;

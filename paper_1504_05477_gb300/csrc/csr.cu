@@ -401,8 +401,10 @@ void csr_product(Exec& ex, const int64_t* row_ptr, const int32_t* col, const flo
         ex.launches += 2;
     }
     const int warps_per_block = 8;
+    if (ex.klog) ex.klog->record(ex.stream);
     spmm_seg_kernel<<<grid_for(nseg_bound, warps_per_block, ex.num_sms), 32 * warps_per_block, 0, ex.stream>>>(
         row_ptr, col, val, seg_off, seg_row, rows, x_rm, c, xp, y_rm, part, corr_kind, cvec, mu, ex.status);
+    if (ex.klog) ex.klog->record(ex.stream);
     spmm_fixup_kernel<<<grid_for(rows * c, 256, ex.num_sms), 256, 0, ex.stream>>>(seg_off, rows, part, c, xp, y_rm,
                                                                                  corr_kind, cvec, mu);
     transpose_in<float>(ex, y_rm, 1, rows, c, xp, Yt, ldy);   // Yt[j][r] = y_rm[r][j]

@@ -257,9 +257,11 @@ cudaError_t launch(Exec& ex, const CUtensorMap& tmA, const CUtensorMap& tmX, con
     cudaError_t err = cudaFuncSetAttribute(bf16_product_kernel<CP, NP>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (err != cudaSuccess) return err;
-    if (ex.klog) ex.klog->record(ex.stream);
+    // the kernel log times the HBM-bound products (X rounded to BF16) only
+    KernelLog* log = NP == 1 ? ex.klog : nullptr;
+    if (log) log->record(ex.stream);
     bf16_product_kernel<CP, NP><<<G, NTHREADS, smem, ex.stream>>>(tmA, tmX, p);
-    if (ex.klog) ex.klog->record(ex.stream);
+    if (log) log->record(ex.stream);
     return cudaGetLastError();
 }
 
