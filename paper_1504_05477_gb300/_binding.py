@@ -33,7 +33,7 @@ class BksOpts(ctypes.Structure):
         ("precision", ctypes.c_int32), ("refine", ctypes.c_int32), ("basis_only", ctypes.c_int32),
         ("sign_fix", ctypes.c_int32), ("jacobi_max_sweeps", ctypes.c_int32),
         ("jacobi_tol", ctypes.c_double), ("profile", ctypes.c_int32),
-        ("product_path", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6),
+        ("product_path", ctypes.c_int32), ("rr_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5),
     ]
 
 

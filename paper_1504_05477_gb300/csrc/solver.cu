@@ -500,6 +500,8 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
     pw.xb_cap = p.xb_cap;
     // Mixed precision (BF16 A): the Krylov products take X rounded to BF16; with refine,
     // B = A^T Q is recomputed FP32-accurately at the full width before Rayleigh-Ritz.
+    // eigen-solve input: R of a d-space block QR of B (rr_mode 1, default) or M = B^T B (2)
+    const bool rr_qr = o.rr_mode != 2;
     const bool bf16_mode = o.precision == BKS_PREC_BF16;
     const bool refine = bf16_mode && o.refine != 0;
     pw.bf16_pieces = bf16_mode ? 1 : 3;
@@ -566,7 +568,7 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
         T* Qprev = krylov ? Qt + size_t(i - 1) * k * p.ldn : Qt;
         T* Bprev = krylov ? Bt + size_t(i - 1) * k * p.ldd : Bt;
         prod(true, Qprev, p.ldn, Bprev, p.ldd, k);       // a2: B_{i-1} = A^T Q_{i-1}
-        if (krylov && !o.basis_only && !refine) orth_b((i - 1) * k, Bprev);
+        if (krylov && !o.basis_only && !refine && rr_qr) orth_b((i - 1) * k, Bprev);
         prod(false, Bprev, p.ldd, W, p.ldn, k);           // a3: W_i = A B_{i-1}
         if (krylov)
             orth(i * k, Qt + size_t(i) * k * p.ldn);     // a4: project + CholeskyQR2
@@ -581,7 +583,7 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
         // a8: B = A^T Q at the full width, FP32-accurate (three BF16 pieces of Q)
         pw.bf16_pieces = 3;
         prod(true, Qt, p.ldn, Bt, p.ldd, w);
-        if (krylov && !o.basis_only)
+        if (krylov && !o.basis_only && rr_qr)
             for (int i = 0; i < q_eff; ++i) orth_b(i * k, Bt + size_t(i) * k * p.ldd);
     }
 
@@ -595,14 +597,16 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
             transpose_in<T>(ex, Bt, sizeof(T) == 8 ? BKS_F64 : BKS_F32, k, d, p.ldd, V, k);
         }
     } else {
-        // a5: M = B^T B is used through a triangular factor: with B = Q_B R (block QR of
-        // the kept blocks), M = R^T R, R = Q_B^T B.  One-sided Jacobi on R^T converges to
-        // U Sigma with U the eigenvectors of M, in fewer sweeps than on M itself and
-        // without accumulating V (Drmac & Veselic's preconditioned Jacobi SVD).
-        orth_b(krylov ? q_eff * k : 0, Blast);
+        // a5: M = B^T B, by default through a triangular factor: with B = Q_B R (block QR
+        // of the kept blocks), M = R^T R, R = Q_B^T B.  One-sided Jacobi on R^T converges
+        // to U Sigma with U the eigenvectors of M, in fewer sweeps than on M itself and
+        // without accumulating V (Drmac & Veselic's preconditioned Jacobi SVD).  With
+        // rr_mode 2 the Jacobi runs on M = B^T B directly (columns converge to U Lambda);
+        // only the order of the column norms is used, so both give the same U.
+        if (rr_qr) orth_b(krylov ? q_eff * k : 0, Blast);
         GemmDesc gm{};
         gm.M = w; gm.N = w; gm.K = d;
-        gm.X = QBt; gm.ldx = p.ldd; gm.Y = Bt; gm.ldy = p.ldd;
+        gm.X = rr_qr ? QBt : Bt; gm.ldx = p.ldd; gm.Y = Bt; gm.ldy = p.ldd;
         gm.y_kmajor = true; gm.y_dtype = sizeof(T) == 8 ? BKS_F64 : BKS_F32;
         gm.out = Rm; gm.ldo = w; gm.alpha = 1.0; gm.beta = 0.0;
         gemm_simt<T>(ex, gm, part, p.part_cap);
