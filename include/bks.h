@@ -87,9 +87,10 @@ typedef struct {
     int32_t product_path;       /* products with a dense A: 0 auto (tensor cores when the
                                    operands meet the TMA alignment rules, else CUDA cores),
                                    1 CUDA cores (SIMT) only */
-    int32_t rr_mode;            /* input of the eigen-solve of M (step 5): 0 auto, 1 the
-                                   triangular factor R of a block QR of B in d-space (M = R^T R,
-                                   one-sided Jacobi on R^T), 2 M = B^T B itself */
+    int32_t rr_mode;            /* input of the eigen-solve of M (step 5): 0 auto (2 for
+                                   w <= 512, else 1), 1 the triangular factor R of a block QR
+                                   of B in d-space (M = R^T R, one-sided Jacobi on R^T), 2 M =
+                                   B^T B itself */
     int32_t reserved[5];
 } bks_opts;
 

@@ -500,8 +500,11 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
     pw.xb_cap = p.xb_cap;
     // Mixed precision (BF16 A): the Krylov products take X rounded to BF16; with refine,
     // B = A^T Q is recomputed FP32-accurately at the full width before Rayleigh-Ritz.
-    // eigen-solve input: R of a d-space block QR of B (rr_mode 1, default) or M = B^T B (2)
-    const bool rr_qr = o.rr_mode != 2;
+    // eigen-solve input: R of a d-space block QR of B (rr_mode 1) or M = B^T B (2).  Auto:
+    // the QR preconditioning saves Jacobi sweeps, which pays for its w / k extra block
+    // orthonormalisations only at large widths (measured: M directly is faster at w = 220
+    // and 450, slower at w = 700)
+    const bool rr_qr = o.rr_mode == 1 || (o.rr_mode == 0 && w > 512);
     const bool bf16_mode = o.precision == BKS_PREC_BF16;
     const bool refine = bf16_mode && o.refine != 0;
     pw.bf16_pieces = bf16_mode ? 1 : 3;
