@@ -83,12 +83,14 @@ __device__ __forceinline__ void circle_pair(int P, int s, int i, int& a, int& b)
     }
 }
 
-// Per-CTA state in shared memory: two slots of b columns, WP values each.
+// Per-CTA state in shared memory: two slots of b columns, WP values each (four when the
+// block moves are double-buffered: parity par selects the pair in use).
 template <typename T>
 struct Blocks {
     T* buf;
     int b, WP;
-    __device__ T* col(int slot, int j) const { return buf + (size_t(slot) * b + j) * WP; }
+    int par;
+    __device__ T* col(int slot, int j) const { return buf + (size_t(par * 2 + slot) * b + j) * WP; }
 };
 
 // Circle-method move of whole blocks between CTAs: top row t_0 stays; t_i -> top i+1
@@ -134,6 +136,39 @@ __device__ void move_blocks(cg::cluster_group& cluster, T* buf, int per_slot, in
         if (src_rank[1] >= 0) blk_id[1] = ids[1];
     }
     __syncthreads();
+}
+
+// The same circle-method move, pushed: each CTA writes its two blocks into the other
+// parity of the receiving CTAs' shared memory (DSMEM stores), then one cluster barrier
+// makes them visible and every CTA switches parity.  The receivers' other parity was
+// last used in the previous round, which the previous barrier closed.
+template <typename T>
+__device__ void push_blocks(cg::cluster_group& cluster, Blocks<T>& B, int* blk_id, int rank, int C, int tid) {
+    int dr[2], ds[2];
+    if (rank == 0) { dr[0] = 0; ds[0] = 0; }
+    else if (rank <= C - 2) { dr[0] = rank + 1; ds[0] = 0; }
+    else { dr[0] = C - 1; ds[0] = 1; }
+    if (rank == 0) { dr[1] = 1; ds[1] = 0; }
+    else { dr[1] = rank - 1; ds[1] = 1; }
+    __syncthreads();
+    const int np = B.par ^ 1;
+    const size_t per_slot = size_t(B.b) * B.WP;
+    for (int slot = 0; slot < 2; ++slot) {
+        const T* src = B.col(slot, 0);
+        T* dst = cluster.map_shared_rank(B.buf, dr[slot]) + size_t(np * 2 + ds[slot]) * per_slot;
+        if (sizeof(T) == 4) {
+            const float4* s4 = reinterpret_cast<const float4*>(src);
+            float4* d4 = reinterpret_cast<float4*>(dst);
+            for (size_t e = tid; e < per_slot / 4; e += blockDim.x) d4[e] = s4[e];
+        } else {
+            const double2* s2 = reinterpret_cast<const double2*>(src);
+            double2* d2 = reinterpret_cast<double2*>(dst);
+            for (size_t e = tid; e < per_slot / 2; e += blockDim.x) d2[e] = s2[e];
+        }
+        if (tid == 0) cluster.map_shared_rank(blk_id, dr[slot])[np * 2 + ds[slot]] = blk_id[B.par * 2 + slot];
+    }
+    cluster.sync();
+    B.par = np;
 }
 
 // Cluster-wide OR of "this CTA rotated during the sweep"; flags live in CTA 0 and
@@ -299,17 +334,20 @@ __device__ void recompute_norms(const Blocks<T>& B, T* nrm2, int warp, int lane)
     }
 }
 
-template <typename T, int E, class Eng>
+template <typename T, int E, class Eng, bool DB>
 __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
     const T* __restrict__ Xin, int64_t ldx, int w, int b, T* Xout, int64_t ldw, int max_sweeps,
     T tol, int* status, int* sweeps_out) {
     constexpr int WP = 32 * E;
-    extern __shared__ unsigned char smem_raw[];
-    Blocks<T> B{reinterpret_cast<T*>(smem_raw), b, WP};
-    T* nrm2 = B.buf + size_t(2) * b * WP;   // squared column norms [slot * b + j]
-    __shared__ int blk_id[2];
+    constexpr int SLOTS = DB ? 4 : 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Blocks<T> B{reinterpret_cast<T*>(smem_raw), b, WP, 0};
+    T* nrm2 = B.buf + size_t(SLOTS) * b * WP;   // squared column norms [slot * b + j]
+    __shared__ int blk_id[4];                   // [parity * 2 + slot]
     __shared__ int rotated_s;
     __shared__ int flags[2][16];
+    __shared__ volatile int step_done[JW];      // cross pairs: last step each warp finished
+    __shared__ int abort_s;
 
     cg::cluster_group cluster = cg::this_cluster();
     const int C = int(cluster.num_blocks());
@@ -331,6 +369,7 @@ __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
         }
     }
     if (tid < 32) flags[tid >> 4][tid & 15] = 0;
+    if (tid == 0) abort_s = 0;
     __syncthreads();
     cluster.sync();
 
@@ -361,23 +400,45 @@ __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
                     __syncthreads();
                 }
             }
-            // cross pairs: a warp keeps slot-0 column j in registers for b sub-rounds
+            // cross pairs: a warp keeps slot-0 column j in registers for b sub-rounds; at
+            // step s it pairs with slot-1 column (j + s) mod b, which the warp of column
+            // j + 1 paired at step s - 1, so it waits only for that warp (bounded)
             for (int j0 = 0; j0 < b; j0 += JW) {
                 const int j = j0 + warp;
                 const bool own = j < b;
+                const int jend = j0 + JW < b ? j0 + JW : b;
+                const int nb = (j + 1) % b;
+                const bool wait_nb = own && nb >= j0 && nb < jend && nb != j;
+                if (lane == 0) step_done[warp] = -1;
+                __syncthreads();
                 typename Eng::Reg r;
                 if (own) Eng::load(r, B.col(0, j), nrm2 + j, lane);
-                for (int s = 0; s < b; ++s) {
-                    if (own) {
-                        const int qj = (j + s) % b;
-                        any |= Eng::pair_reg(r, B.col(1, qj), nrm2 + b + qj, tol, lane);
+                for (int s = 0; s < b && own; ++s) {
+                    if (s > 0 && wait_nb) {
+                        long spins = 0;
+                        while (step_done[nb - j0] < s - 1) {
+                            if (++spins > (1L << 26) || abort_s) {
+                                if (lane == 0 && !abort_s) { atomicOr(status, ST_TIMEOUT); abort_s = 1; }
+                                break;
+                            }
+                        }
+                        __syncwarp();
+                        __threadfence_block();
                     }
-                    __syncthreads();
+                    if (abort_s) break;
+                    const int qj = (j + s) % b;
+                    any |= Eng::pair_reg(r, B.col(1, qj), nrm2 + b + qj, tol, lane);
+                    __syncwarp();
+                    __threadfence_block();
+                    if (lane == 0) step_done[warp] = s;
                 }
                 if (own) Eng::store(r, B.col(0, j), nrm2 + j, lane);
                 __syncthreads();
             }
-            if (C > 1) move_blocks(cluster, B.buf, b * WP, blk_id, rank, C, tid);
+            if (C > 1) {
+                if (DB) push_blocks(cluster, B, blk_id, rank, C, tid);
+                else move_blocks(cluster, B.buf, b * WP, blk_id, rank, C, tid);
+            }
         }
         if (any) rotated_s = 1;
         __syncthreads();
@@ -387,7 +448,7 @@ __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
     if (tid == 0 && rank == 0) *sweeps_out = sweep;
     // write back in original column order
     for (int slot = 0; slot < 2; ++slot) {
-        const int blk = blk_id[slot];
+        const int blk = blk_id[B.par * 2 + slot];
         for (int j = 0; j < b; ++j) {
             const int gc = blk * b + j;
             if (gc >= w) continue;
@@ -445,11 +506,11 @@ struct EngineFor { using type = GenericEngine<T, E>; };
 template <int E>
 struct EngineFor<float, E> { using type = F32x2Engine<E>; };
 
-template <typename T, int E>
+template <typename T, int E, bool DB>
 cudaError_t launch_cluster(cudaStream_t st, int C, size_t smem, const T* Xin, int64_t ldx, int w,
                            int b, T* X, int64_t ldw, int max_sweeps, T tol, int* status,
                            int* sweeps) {
-    auto kern = jacobi_cluster_kernel<T, E, typename EngineFor<T, E>::type>;
+    auto kern = jacobi_cluster_kernel<T, E, typename EngineFor<T, E>::type, DB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
     if (C > 8) {
@@ -508,9 +569,18 @@ void sym_eig(Exec& ex, int w, const T* Xin, int64_t ldx, T* X, int64_t ldw, T* l
     }
     const T ttol = T(tol > 0 ? tol : 4.0 * sqrt(double(w)) * (sizeof(T) == 8 ? 1.1102230246251565e-16
                                                                             : 5.960464477539063e-08));
+    // double-buffered (pushed) block moves when four slots fit in shared memory
+    const size_t smem_db = (size_t(4) * b * 32 * E + size_t(2) * b) * sizeof(T);
+    const bool db = C > 1 && smem_db <= 200 * 1024;
+    if (db) smem = smem_db;
     cudaError_t err = cudaErrorInvalidValue;
-#define BKS_JAC(EE) \
-    case EE: err = launch_cluster<T, EE>(ex.stream, C, smem, Xin, ldx, w, b, X, ldw, max_sweeps, ttol, ex.status, sweeps_dev); break;
+#define BKS_JAC(EE)                                                                                          \
+    case EE:                                                                                                 \
+        err = db ? launch_cluster<T, EE, true>(ex.stream, C, smem, Xin, ldx, w, b, X, ldw, max_sweeps, ttol, \
+                                               ex.status, sweeps_dev)                                        \
+                 : launch_cluster<T, EE, false>(ex.stream, C, smem, Xin, ldx, w, b, X, ldw, max_sweeps, ttol, \
+                                                ex.status, sweeps_dev);                                      \
+        break;
     switch (E) {
         BKS_JAC(2) BKS_JAC(4) BKS_JAC(8) BKS_JAC(12) BKS_JAC(16) BKS_JAC(24) BKS_JAC(32)
     }
