@@ -346,8 +346,7 @@ __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
     __shared__ int blk_id[4];                   // [parity * 2 + slot]
     __shared__ int rotated_s;
     __shared__ int flags[2][16];
-    __shared__ volatile int step_done[JW];      // cross pairs: last step each warp finished
-    __shared__ int abort_s;
+
 
     cg::cluster_group cluster = cg::this_cluster();
     const int C = int(cluster.num_blocks());
@@ -369,7 +368,6 @@ __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
         }
     }
     if (tid < 32) flags[tid >> 4][tid & 15] = 0;
-    if (tid == 0) abort_s = 0;
     __syncthreads();
     cluster.sync();
 
@@ -400,37 +398,18 @@ __global__ void __launch_bounds__(JW * 32) jacobi_cluster_kernel(
                     __syncthreads();
                 }
             }
-            // cross pairs: a warp keeps slot-0 column j in registers for b sub-rounds; at
-            // step s it pairs with slot-1 column (j + s) mod b, which the warp of column
-            // j + 1 paired at step s - 1, so it waits only for that warp (bounded)
+            // cross pairs: a warp keeps slot-0 column j in registers for b sub-rounds
             for (int j0 = 0; j0 < b; j0 += JW) {
                 const int j = j0 + warp;
                 const bool own = j < b;
-                const int jend = j0 + JW < b ? j0 + JW : b;
-                const int nb = (j + 1) % b;
-                const bool wait_nb = own && nb >= j0 && nb < jend && nb != j;
-                if (lane == 0) step_done[warp] = -1;
-                __syncthreads();
                 typename Eng::Reg r;
                 if (own) Eng::load(r, B.col(0, j), nrm2 + j, lane);
-                for (int s = 0; s < b && own; ++s) {
-                    if (s > 0 && wait_nb) {
-                        long spins = 0;
-                        while (step_done[nb - j0] < s - 1) {
-                            if (++spins > (1L << 26) || abort_s) {
-                                if (lane == 0 && !abort_s) { atomicOr(status, ST_TIMEOUT); abort_s = 1; }
-                                break;
-                            }
-                        }
-                        __syncwarp();
-                        __threadfence_block();
+                for (int s = 0; s < b; ++s) {
+                    if (own) {
+                        const int qj = (j + s) % b;
+                        any |= Eng::pair_reg(r, B.col(1, qj), nrm2 + b + qj, tol, lane);
                     }
-                    if (abort_s) break;
-                    const int qj = (j + s) % b;
-                    any |= Eng::pair_reg(r, B.col(1, qj), nrm2 + b + qj, tol, lane);
-                    __syncwarp();
-                    __threadfence_block();
-                    if (lane == 0) step_done[warp] = s;
+                    __syncthreads();
                 }
                 if (own) Eng::store(r, B.col(0, j), nrm2 + j, lane);
                 __syncthreads();
