@@ -32,6 +32,15 @@ constexpr int OP = 2;              // converted A (hi / lo) ring depth
 // shared memory allows, so their L2 round trips overlap
 __host__ __device__ constexpr int x_ring(int cp) { return cp <= 32 ? 4 : 2; }
 constexpr int XR_MAX = 6;
+// Tiles of up to 64 columns take A from tensor memory ("TS" form): the converter writes
+// hi(A) and lo(A) into OPT TMEM stages next to the two accumulators instead of into shared
+// memory, which frees shared memory for a RAT-deep raw A ring.
+__host__ __device__ constexpr bool ts_form(int cp) { return cp <= 64; }
+constexpr int RAT = 10;            // raw A ring depth (TS form)
+constexpr int OPT = 4;             // converted A stages in TMEM (TS form)
+constexpr int ACOL = 256;          // first TMEM column of the A stages (TS form)
+constexpr int RA_MAX = RAT > RA ? RAT : RA;
+constexpr int OP_MAX = OPT > OP ? OPT : OP;
 constexpr int NWARP = 11;
 constexpr int NTHREADS = NWARP * 32;
 constexpr uint32_t TILE_BYTES = BM * KC * 4;   // 16 KB
@@ -40,6 +49,15 @@ constexpr int FLUSH = 4;           // chunks (32 tf32 MMA steps) per TMEM accumu
 // Instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major, M = 128.
 __host__ __device__ constexpr uint32_t idesc_tf32(int n) {
     return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(BM >> 4) << 24);
+}
+// A from tensor memory (TS form): a_tmem is the TMEM address of the A tile's first column.
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate));
 }
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t accumulate) {
@@ -54,8 +72,8 @@ __device__ __forceinline__ float tf32_hi(float v) {
 }
 
 struct Smem {
-    uint64_t raw_full[RA], raw_empty[RA];
-    uint64_t op_empty[OP], conv_full[OP];
+    uint64_t raw_full[RA_MAX], raw_empty[RA_MAX];
+    uint64_t op_empty[OP_MAX], conv_full[OP_MAX];
     uint64_t x_full[XR_MAX], x_empty[XR_MAX];
     uint64_t acc_full[2], acc_empty[2];
     uint64_t drain;
@@ -71,12 +89,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // 1024-byte alignment for the swizzled tiles
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+    constexpr bool TS = ts_form(CP);
+    constexpr int NRA = TS ? RAT : RA;                           // raw A ring depth
+    constexpr int NOP = TS ? OPT : OP;                           // converted A stages
+    constexpr uint32_t ACC_STRIDE = TS ? 2 * CP : 256;           // TMEM columns per accumulator
     const uint32_t b_bytes = uint32_t(2 * CP) * 128u;
-    unsigned char* raw = base;                                   // RA x 16 KB
-    unsigned char* hi = raw + RA * TILE_BYTES;                   // OP x 16 KB
-    unsigned char* lo = hi + OP * TILE_BYTES;                    // OP x 16 KB
+    unsigned char* raw = base;                                   // NRA x 16 KB
+    unsigned char* hi = raw + NRA * TILE_BYTES;                  // OP x 16 KB (shared-memory form)
+    unsigned char* lo = hi + (TS ? 0 : OP) * TILE_BYTES;         // OP x 16 KB (shared-memory form)
     constexpr int XR = x_ring(CP);
-    unsigned char* bop = lo + OP * TILE_BYTES;                   // XR x b_bytes
+    unsigned char* bop = lo + (TS ? 0 : OP) * TILE_BYTES;        // XR x b_bytes
     Smem* sm = reinterpret_cast<Smem*>(bop + XR * b_bytes);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -87,8 +109,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     volatile int* abort_flag = &sm->abort_flag;
 
     if (tid == 0) {
-        for (int i = 0; i < RA; ++i) { mbar_init(&sm->raw_full[i], 1); mbar_init(&sm->raw_empty[i], 4); }
-        for (int i = 0; i < OP; ++i) {
+        for (int i = 0; i < NRA; ++i) { mbar_init(&sm->raw_full[i], 1); mbar_init(&sm->raw_empty[i], 4); }
+        for (int i = 0; i < NOP; ++i) {
             mbar_init(&sm->op_empty[i], 1);
             mbar_init(&sm->conv_full[i], 4);
         }
@@ -116,22 +138,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (warp == 0) {
         // ---------------------------------------------------------------- A producer
         if (lane == 0) {
-            int last[RA];   // phase of the last load issued into each stage (-1: none)
-            for (int s = 0; s < RA; ++s) last[s] = -1;
+            int last[RA_MAX];   // phase of the last load issued into each stage (-1: none)
+            for (int s = 0; s < RA_MAX; ++s) last[s] = -1;
             int64_t i = 0;
             for (int64_t u = ustart; u < uend; ++u, ++i) {
-                const int s = int(i % RA);
-                if (!wait_bar(&sm->raw_empty[s], uint32_t(((i / RA) & 1) ^ 1), abort_flag, p.status)) break;
+                const int s = int(i % NRA);
+                if (!wait_bar(&sm->raw_empty[s], uint32_t(((i / NRA) & 1) ^ 1), abort_flag, p.status)) break;
                 const int64_t t = u / p.cpt, kc = u % p.cpt;
                 mbar_expect_tx(&sm->raw_full[s], TILE_BYTES);
                 if (p.mode == 0)   // AX: box {32 (d), 128 (n)}
                     tma_load_2d(raw + s * TILE_BYTES, &tmA, int(kc * KC), int(t * BM), &sm->raw_full[s]);
                 else               // ATX: box {128 (d), 32 (n)}
                     tma_load_2d(raw + s * TILE_BYTES, &tmA, int(t * BM), int(kc * KC), &sm->raw_full[s]);
-                last[s] = int((i / RA) & 1);
+                last[s] = int((i / NRA) & 1);
             }
             // every load issued has landed before shared memory is released (bounded)
-            for (int s = 0; s < RA; ++s) drain_bar(&sm->raw_full[s], last[s]);
+            for (int s = 0; s < NRA; ++s) drain_bar(&sm->raw_full[s], last[s]);
         }
     } else if (warp == 1) {
         // ---------------------------------------------------------------- X producer
@@ -167,20 +189,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     first = true;
                 }
                 (void)t;
-                const int o = int(i % OP), xs = int(i % XR);
-                const uint32_t par = uint32_t((i / OP) & 1);
+                const int o = int(i % NOP), xs = int(i % XR);
+                const uint32_t par = uint32_t((i / NOP) & 1);
                 if (!wait_bar(&sm->conv_full[o], par, abort_flag, p.status)) break;
                 if (!wait_bar(&sm->x_full[xs], uint32_t((i / XR) & 1), abort_flag, p.status)) break;
                 tc_fence_after();
-                const uint32_t d_tmem = tmem + uint32_t((sub & 1) * 256);
-                const uint64_t dh = desc_sw128(smem_u32(hi + o * TILE_BYTES));
-                const uint64_t dl = desc_sw128(smem_u32(lo + o * TILE_BYTES));
+                const uint32_t d_tmem = tmem + uint32_t(sub & 1) * ACC_STRIDE;
                 const uint64_t db = desc_sw128(smem_u32(bop + xs * b_bytes));
+                if constexpr (TS) {
+                    // A stage o: hi(A) in columns [0, 32), lo(A) in [32, 64), one column per K
+                    const uint32_t a_hi = tmem + uint32_t(ACOL + o * 64), a_lo = a_hi + 32;
 #pragma unroll
-                for (int kk = 0; kk < KC / 8; ++kk) {   // K = 8 per tf32 MMA = 32 bytes
-                    const uint64_t adv = uint64_t(kk * 2);
-                    mma_tf32(d_tmem, dh + adv, db + adv, id_full, (first && kk == 0) ? 0u : 1u);
-                    mma_tf32(d_tmem, dl + adv, db + adv, id_half, 1u);
+                    for (int kk = 0; kk < KC / 8; ++kk) {   // K = 8 per tf32 MMA
+                        const uint64_t adv = uint64_t(kk * 2);
+                        mma_tf32_ts(d_tmem, a_hi + uint32_t(kk * 8), db + adv, id_full, (first && kk == 0) ? 0u : 1u);
+                        mma_tf32_ts(d_tmem, a_lo + uint32_t(kk * 8), db + adv, id_half, 1u);
+                    }
+                } else {
+                    const uint64_t dh = desc_sw128(smem_u32(hi + o * TILE_BYTES));
+                    const uint64_t dl = desc_sw128(smem_u32(lo + o * TILE_BYTES));
+#pragma unroll
+                    for (int kk = 0; kk < KC / 8; ++kk) {   // K = 8 per tf32 MMA = 32 bytes
+                        const uint64_t adv = uint64_t(kk * 2);
+                        mma_tf32(d_tmem, dh + adv, db + adv, id_full, (first && kk == 0) ? 0u : 1u);
+                        mma_tf32(d_tmem, dl + adv, db + adv, id_half, 1u);
+                    }
                 }
                 first = false;
                 umma_commit(&sm->op_empty[o]);
@@ -196,6 +229,51 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ---------------------------------------------------------------- converters
         const int ct = tid - 96;   // 0..127
         int64_t i = 0;
+        if constexpr (TS) {
+            // thread = TMEM lane = row m of the A tile (a warp reaches lanes 32 (warp % 4) ..)
+            const int m = (warp & 3) * 32 + lane;
+            const uint32_t lane_addr = uint32_t((warp & 3) * 32) << 16;
+            for (int64_t u = ustart; u < uend; ++u, ++i) {
+                const int s = int(i % NRA), o = int(i % NOP);
+                if (!wait_bar(&sm->raw_full[s], uint32_t((i / NRA) & 1), abort_flag, p.status)) break;
+                const unsigned char* rs = raw + s * TILE_BYTES;
+                uint32_t h[32], l[32];
+                if (p.mode == 0) {   // 128B-swizzled K-major raw tile: row m's eight 16-byte chunks
+                    const int rowoff = (m >> 3) * 1024 + (m & 7) * 128;
+#pragma unroll
+                    for (int g = 0; g < 8; ++g) {
+                        const float4 v = *reinterpret_cast<const float4*>(rs + rowoff + ((g ^ (m & 7)) << 4));
+                        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float hv = tf32_hi(vv[e]);
+                            h[4 * g + e] = __float_as_uint(hv);
+                            l[4 * g + e] = __float_as_uint(vv[e] - hv);
+                        }
+                    }
+                } else {             // raw tile: 32 contraction rows x 128 columns (row pitch 512 B)
+                    const float* rf = reinterpret_cast<const float*>(rs);
+#pragma unroll
+                    for (int kk = 0; kk < 32; ++kk) {
+                        const float v = rf[kk * BM + m];
+                        const float hv = tf32_hi(v);
+                        h[kk] = __float_as_uint(hv);
+                        l[kk] = __float_as_uint(v - hv);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm->raw_empty[s]);   // the raw tile is in registers
+                if (!wait_bar(&sm->op_empty[o], uint32_t(((i / NOP) & 1) ^ 1), abort_flag, p.status)) break;
+                tc_fence_after();
+                const uint32_t col = tmem + lane_addr + uint32_t(ACOL + o * 64);
+                tmem_st32(col, h);
+                tmem_st32(col + 32, l);
+                tmem_wait_st();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm->conv_full[o]);
+            }
+        } else
         for (int64_t u = ustart; u < uend; ++u, ++i) {
             const int s = int(i % RA), o = int(i % OP);
             if (!wait_bar(&sm->raw_full[s], uint32_t((i / RA) & 1), abort_flag, p.status)) break;
@@ -269,7 +347,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t acc = tmem + uint32_t((sub & 1) * 256) + (uint32_t(grp * 32) << 16);
+                const uint32_t acc = tmem + uint32_t(sub & 1) * ACC_STRIDE + (uint32_t(grp * 32) << 16);
                 if constexpr (CP <= 64) {   // hi.hi and hi.lo halves, one wait per 32 columns
 #pragma unroll
                     for (int j0 = 0; j0 < CP; j0 += 32) {
@@ -433,6 +511,8 @@ int64_t partial_floats(int64_t rows_out, int64_t len, int kc, int cp, int num_sm
 }
 
 size_t smem_bytes(int cp) {
+    if (ts_form(cp))
+        return size_t(RAT) * TILE_BYTES + size_t(x_ring(cp)) * 2 * cp * 128 + sizeof(Smem) + 1024;
     return size_t(RA) * TILE_BYTES + size_t(2 * OP) * TILE_BYTES + size_t(x_ring(cp)) * 2 * cp * 128 +
            sizeof(Smem) + 1024;
 }
