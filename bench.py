@@ -321,6 +321,24 @@ def sparse_cpu_baseline(rp, ci, cv, mu, d, k, q):
                       "(scipy sparse products single-threaded)"}
 
 
+def job_time(ms_local, world, device=None):
+    """Whole-job time of a step: the maximum over ranks of each rank's measured time (the
+    slowest replica decides when all solves are done).  Collective on every rank."""
+    if world <= 1:
+        return ms_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def per_solve(ms_per_step, world, units):
+    """ms per solve over the whole job: every step each of the `world` ranks finishes
+    `units` solves, all within the (max-over-ranks) step time."""
+    return ms_per_step / (world * units)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -360,13 +378,9 @@ def main():
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
-    ms_total = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = job_time(ev0.elapsed_time(ev1), world, dev)
     ms_per_step = ms_total / args.steps
-    value = ms_per_step / (world * w.units)   # ms per solve over all ranks and matrices
+    value = per_solve(ms_per_step, world, w.units)   # ms per solve over all ranks and matrices
 
     hbm_peak, _, peak_src = peaks()
     nprod = 2 * w.q + 2
@@ -421,7 +435,7 @@ def main():
     for i in range(e2e_steps):
         h2d, d2h = w.e2e(dev, 200 + i)
     barrier()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps / (world * w.units)
+    e2e_ms = per_solve(job_time((time.perf_counter() - t0) * 1e3, world, dev) / e2e_steps, world, w.units)
 
     if rank != 0:
         if world > 1:
