@@ -91,7 +91,12 @@ typedef struct {
                                    w <= 512, else 1), 1 the triangular factor R of a block QR
                                    of B in d-space (M = R^T R, one-sided Jacobi on R^T), 2 M =
                                    B^T B itself */
-    int32_t reserved[5];
+    int32_t eig_mode;           /* eigen-solve of M (step 6): 0 auto (when only the k leading
+                                   vectors are returned and w > k: Householder tridiagonal form
+                                   of M = B^T B, multisection and inverse iteration, if w fits
+                                   its kernels; otherwise the one-sided Jacobi), 1 always the
+                                   one-sided Jacobi */
+    int32_t reserved[4];
 } bks_opts;
 
 typedef struct {
@@ -111,7 +116,8 @@ typedef struct {
                                    dominant product kernel alone (dense FP32: the tensor-core
                                    kernel; BF16: its BF16-rounded products; CSR: the SpMM) */
     int32_t product_kernel_launches;
-    int32_t reserved[6];
+    int32_t eig_path;           /* eigen-solve that ran: 0 one-sided Jacobi, 1 tridiagonal */
+    int32_t reserved[5];
 } bks_stats;
 
 typedef struct bks_ctx bks_ctx;

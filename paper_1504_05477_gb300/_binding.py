@@ -33,7 +33,8 @@ class BksOpts(ctypes.Structure):
         ("precision", ctypes.c_int32), ("refine", ctypes.c_int32), ("basis_only", ctypes.c_int32),
         ("sign_fix", ctypes.c_int32), ("jacobi_max_sweeps", ctypes.c_int32),
         ("jacobi_tol", ctypes.c_double), ("profile", ctypes.c_int32),
-        ("product_path", ctypes.c_int32), ("rr_mode", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5),
+        ("product_path", ctypes.c_int32), ("rr_mode", ctypes.c_int32), ("eig_mode", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 
@@ -46,7 +47,7 @@ class BksStats(ctypes.Structure):
         ("ms_total", ctypes.c_float),
         ("product_bytes", ctypes.c_double), ("product_flops", ctypes.c_double),
         ("ms_product_kernel", ctypes.c_float), ("product_kernel_launches", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 6),
+        ("eig_path", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5),
     ]
 
     def as_dict(self):

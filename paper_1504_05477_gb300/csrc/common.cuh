@@ -183,6 +183,19 @@ template <typename T>
 void sym_eig(Exec& ex, int w, const T* Xin, int64_t ldx, T* X, int64_t ldw, T* lam, T* nrm,
              T* Vt, int64_t ldv, int* order, int max_sweeps, double tol, int* sweeps_dev);
 
+// Eigenvectors of the m largest eigenvalues of the symmetric w x w M (row pitch w) by
+// Householder tridiagonalisation, multisection, inverse iteration and one CholeskyQR2
+// (orth_block with `ows`, sized for blocks of m columns at least w long): row i of Vt
+// (pitch ldv) = eigenvector of the i-th largest eigenvalue.  `scratch`:
+// tridiag_scratch_elems elements of T.  False (nothing launched) when the sizes do not
+// fit its kernels.
+template <typename T>
+bool tridiag_fits(int w, int m);
+size_t tridiag_scratch_elems(int w, int m);
+struct OrthWs;
+template <typename T>
+bool topk_tridiag(Exec& ex, int w, const T* M, int m, T* Vt, int64_t ldv, T* scratch, const OrthWs& ows);
+
 // Column-wise argmax |.| sign normalisation of a row-major n x k matrix (and the
 // matching rows of Ut, k x ldu).
 template <typename T>

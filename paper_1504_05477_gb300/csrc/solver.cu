@@ -26,6 +26,7 @@ struct PendingSolve {
     int q_eff = 0, w = 0;
     bool deflated = false, basis_only = false;
     int launches = 0, product_launches = 0;
+    int eig_path = 0;
     double product_bytes = 0, product_flops = 0;
 };
 
@@ -286,6 +287,7 @@ struct Plan {
     int64_t tpart_cap, xb_cap;
     bool sparse;
     CsrLayout csr;
+    size_t td;               // scratch of the tridiagonal eigen-solve (0 bytes when it cannot run)
     size_t Qt, Bt, QBt, Pit, W, Wtmp, Wb, Wbtmp, part, og, rfac, ct, Rm, JX, lam, nrm, Vt,
         order, Vk, stat, fpart, fgram, fbar;
     int64_t fcap;
@@ -347,6 +349,10 @@ Plan make_plan(const bks_matrix* A, int k, int q_eff, int w, size_t tb, int sms,
     p.Vt = a.take(size_t(w) * w * tb);
     p.order = a.take(size_t(w) * sizeof(int));
     p.Vk = a.take(size_t(kout) * p.ldd * tb);
+    {
+        const bool fits = tb == 4 ? tridiag_fits<float>(w, kout) : tridiag_fits<double>(w, kout);
+        p.td = a.take(fits ? tridiag_scratch_elems(w, kout) * tb : 0);
+    }
     const int64_t ldmax = p.ldn > p.ldd ? p.ldn : p.ldd;
     p.xh = a.take(size_t(k) * ldmax * 4);
     p.xl = a.take(size_t(k) * ldmax * 4);
@@ -429,6 +435,7 @@ bks_status finish_solve(bks_ctx* ctx, bks_stats* st) {
         st->product_launches = ps.product_launches;
         st->product_bytes = ps.product_bytes;
         st->product_flops = ps.product_flops;
+        st->eig_path = ps.eig_path;
     }
     if (status & ST_TIMEOUT) return fail(ctx, BKS_ERR_TIMEOUT, "a bounded device-side wait gave up");
     if (status & ST_BADINPUT) return fail(ctx, BKS_ERR_INVALID_ARG, "CSR structure check failed");
@@ -504,7 +511,12 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
     // the QR preconditioning saves Jacobi sweeps, which pays for its w / k extra block
     // orthonormalisations only at large widths (measured: M directly is faster at w = 220
     // and 450, slower at w = 700)
-    const bool rr_qr = o.rr_mode == 1 || (o.rr_mode == 0 && w > 512);
+    // Eigen-solve: only Ubar_k is needed, so by default M = B^T B goes through the
+    // tridiagonal top-k solver; the one-sided Jacobi covers Ritz triplets (all w vectors),
+    // SI (w = k), widths beyond the tridiagonal kernels and eig_mode 1.
+    const bool use_td = !o.basis_only && !triplets && o.eig_mode != 1 && o.rr_mode != 1 && k < w &&
+                        tridiag_fits<T>(w, k);
+    const bool rr_qr = !use_td && (o.rr_mode == 1 || (o.rr_mode == 0 && w > 512));
     const bool bf16_mode = o.precision == BKS_PREC_BF16;
     const bool refine = bf16_mode && o.refine != 0;
     pw.bf16_pieces = bf16_mode ? 1 : 3;
@@ -591,6 +603,7 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
     }
 
     const int t_rr = prof.begin();
+    int eig_path = 0;
     if (o.basis_only) {
         // Z = first k columns of Q (Sec. 4.1: enough for low-rank approximation)
         transpose_in<T>(ex, Qt, sizeof(T) == 8 ? BKS_F64 : BKS_F32, k, n, p.ldn, Z, k);
@@ -615,8 +628,10 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
         gemm_simt<T>(ex, gm, part, p.part_cap);
         check_finite<T>(ex, Rm, int64_t(w) * w);
         // a6: eigen-decomposition of M, descending (row j of Rm is column j of R^T)
-        sym_eig<T>(ex, w, Rm, w, JX, w, lam, nrm, Vt, w, order,
-                   o.jacobi_max_sweeps > 0 ? o.jacobi_max_sweeps : 40, o.jacobi_tol, stat + 1);
+        const int sweeps = o.jacobi_max_sweeps > 0 ? o.jacobi_max_sweeps : 40;
+        eig_path = use_td && topk_tridiag<T>(ex, w, Rm, k, Vt, w, reinterpret_cast<T*>(base + p.td), ows) ? 1 : 0;
+        if (eig_path == 0)
+            sym_eig<T>(ex, w, Rm, w, JX, w, lam, nrm, Vt, w, order, sweeps, o.jacobi_tol, stat + 1);
         // a7: Z = Q Ubar_k (row-major n x k)
         GemmDesc gz{};
         gz.M = kout; gz.N = n; gz.K = w;
@@ -649,6 +664,7 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
     ps.deflated = deflated;
     ps.basis_only = o.basis_only != 0;
     ps.launches = ex.launches;
+    ps.eig_path = eig_path;
     ps.product_launches = ex.product_launches;
     {
         const int nprod = 2 * q_eff + 2;   // q+1 products with A, q+1 with A^T (both methods)
