@@ -66,7 +66,8 @@ TdShape td_shape(int w, int C) {
     return s;
 }
 
-// Smallest power-of-two cluster with at most 64 columns per CTA (else the fewest that fit).
+// Smallest power-of-two cluster with at most 32 columns per CTA (else the widest that fits;
+// measured on GB300: 32 columns per CTA beat 64 and 128 at w = 220 and 450).
 template <typename T>
 TdShape td_pick(int w) {
     TdShape best;
@@ -74,20 +75,21 @@ TdShape td_pick(int w) {
         const TdShape s = td_shape<T>(w, C);
         if (s.C == 0 || s.smem > SMEM_MAX) continue;
         best = s;
-        if (s.nl <= 64) break;
+        if (s.nl <= 32) break;
     }
     return best;
 }
 
 // Householder tridiagonalisation of the symmetric w x w M (row pitch w), scaled by
 // 1 / max_i M_ii.  CTA r keeps columns c = l C + r (l < nl).  Step j: every CTA holds
-// column j (rows j..w-1) in xv and builds the same reflector H_j = I - tau v v^T
-// (v[j+1] = 1; all CTAs compute it in the same order, so bit for bit); tpc threads per
-// own column c > j form p_c = tau A(j+1:, c) . v; the owner of column j+1 publishes it.
-// After the cluster barrier each CTA gathers p, K = (tau / 2) p . v, w = p - K v,
-// updates its columns, A -= v w^T + w v^T, and the published column, the next xv.
-// Outputs: dT (w), eT (w - 1), tau (w - 1) and the reflectors: row j of V holds v_j in
-// columns j+1..w-1.
+// column j (rows j..w-1) in xa and derives the same reflector H_j = I - tau v v^T from it
+// (v[j+1] = 1, v_i = s x_i below; all CTAs compute it in the same order, so bit for bit);
+// tpc threads per own column c > j form p_c = tau A(j+1:, c) . v; the owner of column
+// j+1 publishes it.  After the cluster barrier each CTA gathers p, K = (tau / 2) p . v,
+// w = p - K v, updates its columns, A -= v w^T + w v^T, and the published column, which
+// becomes the next step's xa (double-buffered).  Per step: one cluster barrier and two
+// CTA barriers.  Outputs: dT (w), eT (w - 1), tau (w - 1) and the reflectors: row j of V
+// holds v_j in columns j+1..w-1.
 template <typename T>
 __global__ void __launch_bounds__(TD_NT) tridiag_kernel(const T* __restrict__ M, int w, int tpc, int64_t wp,
                                                         T* __restrict__ dT, T* __restrict__ eT,
@@ -100,9 +102,8 @@ __global__ void __launch_bounds__(TD_NT) tridiag_kernel(const T* __restrict__ M,
     const int nlp = (nl + 3) / 4 * 4;
     extern __shared__ __align__(16) unsigned char td_smem_raw[];
     T* A = reinterpret_cast<T*>(td_smem_raw);   // nl x wp
-    T* xv = A + size_t(nl) * wp;
-    T* vv = xv + wp;
-    T* pv = vv + wp;                            // gathered p (raw)
+    T* xv = A + size_t(nl) * wp;                // 2 x wp: current column, next column
+    T* pv = xv + 2 * wp;                        // gathered p (raw)
     T* cbuf = pv + wp;                          // 2 x wp: published column
     T* pbuf = cbuf + 2 * wp;                    // 2 x nlp: p of the own columns
     T* red2 = pbuf + 2 * nlp;                   // 2 x TD_NW: warp partials of p . v
@@ -145,47 +146,49 @@ __global__ void __launch_bounds__(TD_NT) tridiag_kernel(const T* __restrict__ M,
     __syncthreads();
 
     for (int j = 0;; ++j) {
-        if (r == 0 && tid == 0) dT[j] = xv[j];
-        if (j == w - 1) break;
         const int par = j & 1;
-        // reflector from rows j+1.. of column j (beta = -sign(alpha) |x|)
+        const T* xa = xv + par * wp;            // column j
+        T* xb = xv + (par ^ 1) * wp;            // column j+1 after this step
+        if (r == 0 && tid == 0) dT[j] = xa[j];
+        if (j == w - 1) break;
+        // reflector from rows j+1.. of column j (beta = -sign(alpha) |x|), v_i = scal x_i
         T ss = T(0);
         for (int q = 0; q < TD_NW; ++q) ss += red[q];
-        const T alpha = xv[j + 1];
-        T tau = T(0), beta = alpha;
+        const T alpha = xa[j + 1];
+        T tau = T(0), beta = alpha, scal = T(0);
         if (ss > T(0)) {
             beta = -copysign(sqrt(alpha * alpha + ss), alpha);
             tau = (beta - alpha) / beta;
-            const T scal = T(1) / (alpha - beta);
-            for (int i = j + 2 + tid; i < w; i += TD_NT) vv[i] = xv[i] * scal;
-            if (tid == 0) vv[j + 1] = T(1);
+            scal = T(1) / (alpha - beta);
         }
-        if (r == 0 && tid == 0) {
-            eT[j] = beta;
-            tau_out[j] = tau;
-        }
-        __syncthreads();   // (1) vv complete; red consumed
         const bool act = tau != T(0);
-        if (r == 0)
-            for (int i = j + 1 + tid; i < w; i += TD_NT) V[int64_t(j) * w + i] = act ? vv[i] : T(0);
+        if (r == 0) {
+            if (tid == 0) {
+                eT[j] = beta;
+                tau_out[j] = tau;
+            }
+            for (int i = j + 1 + tid; i < w; i += TD_NT)
+                V[int64_t(j) * w + i] = act ? (i == j + 1 ? T(1) : xa[i] * scal) : T(0);
+        }
         if (act) {
+            // p_c = tau (A(j+1, c) + scal sum_{i >= j+2} A(i, c) x_i)
             T s0 = T(0), s1 = T(0);
+            const T* col = A + lt * wp;
             if (colv && ct > j) {
-                const T* col = A + lt * wp;
-                int i = j + 1 + sub;
+                int i = j + 2 + sub;
                 for (; i + tpc < w; i += 2 * tpc) {
-                    s0 += col[i] * vv[i];
-                    s1 += col[i + tpc] * vv[i + tpc];
+                    s0 += col[i] * xa[i];
+                    s1 += col[i + tpc] * xa[i + tpc];
                 }
-                if (i < w) s0 += col[i] * vv[i];
+                if (i < w) s0 += col[i] * xa[i];
             }
             T s = s0 + s1;
             for (int o = tpc >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            s *= tau;
             T dp = T(0);
             if (colv && ct > j && sub == 0) {
+                s = tau * (col[j + 1] + scal * s);
                 pbuf[par * nlp + lt] = s;
-                dp = s * vv[ct];
+                dp = s * (ct == j + 1 ? T(1) : xa[ct] * scal);
             }
             dp = warp_sum(dp);
             if (lane == 0) red2[par * TD_NW + warp] = dp;
@@ -195,7 +198,7 @@ __global__ void __launch_bounds__(TD_NT) tridiag_kernel(const T* __restrict__ M,
             const T* col = A + ((j + 1) >> lc) * wp;
             for (int i = j + 1 + tid; i < w; i += TD_NT) cbuf[par * wp + i] = col[i];
         }
-        cl.sync();   // (2)
+        cl.sync();
         const T* ycol = cl.map_shared_rank(cbuf + par * wp, own1);
         T ssn = T(0);
         if (act) {
@@ -208,33 +211,33 @@ __global__ void __launch_bounds__(TD_NT) tridiag_kernel(const T* __restrict__ M,
                 dsum = warp_sum(dsum);
                 if (lane == 0) misc[0] = T(0.5) * tau * dsum;
             }
-            __syncthreads();   // (3) pv, K
+            __syncthreads();   // pv, K
             const T K = misc[0];
             const T w1 = pv[j + 1] - K;   // v[j+1] = 1
             for (int i = j + 1 + tid; i < w; i += TD_NT) {
-                const T vi = vv[i];
+                const T vi = i == j + 1 ? T(1) : xa[i] * scal;
                 const T x = ycol[i] - (vi * w1 + (pv[i] - K * vi));
-                xv[i] = x;
+                xb[i] = x;
                 if (i >= j + 3) ssn += x * x;
             }
             if (colv && ct > j + 1) {
-                const T vc = vv[ct], wc = pv[ct] - K * vc;
+                const T vc = xa[ct] * scal, wc = pv[ct] - K * vc;
                 T* col = A + lt * wp;
                 for (int i = j + 2 + sub; i < w; i += tpc) {
-                    const T vi = vv[i];
+                    const T vi = xa[i] * scal;
                     col[i] -= vi * wc + (pv[i] - K * vi) * vc;
                 }
             }
         } else {
             for (int i = j + 1 + tid; i < w; i += TD_NT) {
                 const T x = ycol[i];
-                xv[i] = x;
+                xb[i] = x;
                 if (i >= j + 3) ssn += x * x;
             }
         }
         ssn = warp_sum(ssn);
         if (lane == 0) red[warp] = ssn;
-        __syncthreads();   // (4)
+        __syncthreads();
     }
     cl.sync();   // no CTA leaves while another may still read its shared memory
 }
