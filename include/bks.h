@@ -87,10 +87,10 @@ typedef struct {
     int32_t product_path;       /* products with a dense A: 0 auto (tensor cores when the
                                    operands meet the TMA alignment rules, else CUDA cores),
                                    1 CUDA cores (SIMT) only */
-    int32_t rr_mode;            /* input of the eigen-solve of M (step 5): 0 auto (2 for
-                                   w <= 512, else 1), 1 the triangular factor R of a block QR
-                                   of B in d-space (M = R^T R, one-sided Jacobi on R^T), 2 M =
-                                   B^T B itself */
+    int32_t rr_mode;            /* input of the eigen-solve of M (step 5): 0 auto (M = B^T B
+                                   for the tridiagonal solver and for the Jacobi at w <= 512,
+                                   else 1), 1 the triangular factor R of a block QR of B in
+                                   d-space (M = R^T R, one-sided Jacobi on R^T), 2 M = B^T B */
     int32_t eig_mode;           /* eigen-solve of M (step 6): 0 auto (when only the k leading
                                    vectors are returned and w > k: Householder tridiagonal form
                                    of M = B^T B, multisection and inverse iteration, if w fits
