@@ -96,7 +96,14 @@ typedef struct {
                                    of M = B^T B, multisection and inverse iteration, if w fits
                                    its kernels; otherwise the one-sided Jacobi), 1 always the
                                    one-sided Jacobi */
-    int32_t reserved[4];
+    int32_t block_p;            /* columns p of Pi and width of every Krylov block (Sec. 8,
+                                   "Improved Convergence With Spectral Decay": any p >= k, with
+                                   q iterations depending on sigma_k / sigma_{p+1}); 0 = k.  The
+                                   call still returns the k leading Ritz vectors; w = p (q + 1)
+                                   (BKI) or p (SI), q capped so that w <= min(n, d); a caller-
+                                   supplied Pi is d x p.  Must be 0 or in [k, min(n, d)], at
+                                   most 128; Ritz triplets take p = k */
+    int32_t reserved[3];
 } bks_opts;
 
 typedef struct {

@@ -19,6 +19,9 @@ Readings of the paper taken here (each listed in the design notes):
   q_eff = min(q, floor(min(n, d)/k) - 1).
 * Each Ritz vector's sign is fixed so that its entry of largest magnitude is
   positive (lowest index on ties).
+* Pi may have p >= k columns (Sec. 8, "Improved Convergence With Spectral Decay"):
+  every block then has p columns, w = p(q+1) (q capped with p in place of k), and the
+  k leading Ritz vectors are returned.
 """
 from __future__ import annotations
 
@@ -125,6 +128,15 @@ def _rayleigh_ritz(q_mat: np.ndarray, b_mat: np.ndarray, k: int, q_eff: int) -> 
     return Result(z, sigma, q_mat, b_mat, m, lam, ub, q_eff)
 
 
+def _start_block(pi, d: int, k: int) -> np.ndarray:
+    """Pi as FP64, d x p with p >= k columns (p = k in Algorithms 1 and 2, any p >= k in
+    Sec. 8)."""
+    pi64 = np.asarray(pi, dtype=np.float64)
+    if pi64.ndim != 2 or pi64.shape[0] != d or pi64.shape[1] < k:
+        raise ValueError(f"Pi must be {d} x p with p >= {k}, got {pi64.shape}")
+    return pi64
+
+
 def block_krylov(a, k: int, q: int, pi) -> Result:
     """Algorithm 2 (Block Krylov Iteration), FP64.
 
@@ -134,10 +146,8 @@ def block_krylov(a, k: int, q: int, pi) -> Result:
     space as the paper's explicit K.  B_i = A^T Q_i is kept and M = B^T B.
     """
     op = _as_op(a)
-    pi64 = np.asarray(pi, dtype=np.float64)
-    if pi64.shape != (op.d, k):
-        raise ValueError(f"Pi must be {op.d} x {k}, got {pi64.shape}")
-    q_eff = q_effective(op.n, op.d, k, q)
+    pi64 = _start_block(pi, op.d, k)
+    q_eff = q_effective(op.n, op.d, pi64.shape[1], q)
     qs = [orthonormalise(op.mul(pi64))]
     bs = []
     for _ in range(q_eff):
@@ -156,9 +166,7 @@ def simul_iter(a, k: int, q: int, pi) -> Result:
     """Algorithm 1 (Simultaneous Iteration), FP64, orthonormalised after every
     iteration (Sec. 4.1): Q <- orth(A A^T Q), starting from Q = orth(A Pi)."""
     op = _as_op(a)
-    pi64 = np.asarray(pi, dtype=np.float64)
-    if pi64.shape != (op.d, k):
-        raise ValueError(f"Pi must be {op.d} x {k}, got {pi64.shape}")
+    pi64 = _start_block(pi, op.d, k)
     qm = orthonormalise(op.mul(pi64))
     for _ in range(q):
         qm = orthonormalise(op.mul(op.tmul(qm)))

@@ -152,7 +152,7 @@ def _as_bks(a, precision="auto"):
 
 
 def _opts(precision="auto", basis_only=False, sign_fix=True, profile=False, jacobi_tol=0.0,
-          jacobi_max_sweeps=40, refine=True, simt=False, rr_mode="auto", eig_mode="auto"):
+          jacobi_max_sweeps=40, refine=True, simt=False, rr_mode="auto", eig_mode="auto", block_p=0):
     o = BksOpts()
     B.load().bks_opts_default(ctypes.byref(o))
     o.precision = {"auto": B.PREC_AUTO, "f64": B.PREC_F64, "f32": B.PREC_F32,
@@ -166,6 +166,7 @@ def _opts(precision="auto", basis_only=False, sign_fix=True, profile=False, jaco
     o.product_path = 1 if simt else 0
     o.rr_mode = {"auto": 0, "qr": 1, "gram": 2}[rr_mode]
     o.eig_mode = {"auto": 0, "jacobi": 1}[eig_mode]
+    o.block_p = int(block_p)
     return o
 
 
@@ -185,8 +186,9 @@ def _solve(fn_name, a, k, q, seed, pi, want_v, precision, stats, **kw):
     sig = torch.empty((k,), dtype=odt, device=dev)
     v = torch.empty((d, k), dtype=odt, device=dev) if want_v else None
     if pi is not None:
-        if pi.shape != (d, k) or pi.dtype != odt or not pi.is_contiguous() or pi.device != z.device:
-            raise ValueError(f"pi must be a contiguous {d}x{k} {odt} tensor on {z.device}")
+        pc = kw.get("block_p") or k
+        if pi.shape != (d, pc) or pi.dtype != odt or not pi.is_contiguous() or pi.device != z.device:
+            raise ValueError(f"pi must be a contiguous {d}x{pc} {odt} tensor on {z.device}")
     opts = _opts(precision=precision, **kw)
     st = BksStats()
     fn = getattr(ctx.lib, fn_name)
@@ -203,7 +205,8 @@ def _solve(fn_name, a, k, q, seed, pi, want_v, precision, stats, **kw):
 def block_krylov(a, k, q, seed=0, pi=None, want_v=False, precision="auto", stats=False, **kw):
     """Algorithm 2 (Block Krylov Iteration) on a CUDA matrix A (n x d).  Returns
     Z (n x k, orthonormal Ritz vectors) and sigma (k Ritz values, descending); with
-    want_v also V (d x k); with stats also a dict of bks_stats."""
+    want_v also V (d x k); with stats also a dict of bks_stats.  block_p = p > k runs the
+    iteration with p columns in Pi and in every block (Sec. 8); pi is then d x p."""
     return _solve("bks_block_krylov", a, k, q, seed, pi, want_v, precision, stats, **kw)
 
 
@@ -428,8 +431,9 @@ def block_krylov_batched(mats, k, q, seeds=None, pis=None, want_v=False, precisi
             vp[i] = v.data_ptr()
         if pis is not None and pis[i] is not None:
             p = pis[i]
-            if p.shape != (m.d, k) or p.dtype != odt or not p.is_contiguous():
-                raise ValueError(f"pis[{i}] must be a contiguous {m.d}x{k} {odt} tensor")
+            pc = kw.get("block_p") or k
+            if p.shape != (m.d, pc) or p.dtype != odt or not p.is_contiguous():
+                raise ValueError(f"pis[{i}] must be a contiguous {m.d}x{pc} {odt} tensor")
             pp[i] = p.data_ptr()
         outs.append((z, s, v) if want_v else (z, s))
     ctx = context(dev)

@@ -449,10 +449,12 @@ bks_status finish_solve(bks_ctx* ctx, bks_stats* st) {
 }
 
 template <typename T>
-bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed, const void* pi,
+bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed, const void* pi,
                  void* Zv, void* sigv, void* Vv, const bks_opts& o, bks_stats* st, bool krylov,
                  bool triplets, bool defer) {
     const int64_t n = A->n, d = A->d;
+    // block size: the p >= kz columns of Pi (Sec. 8, spectral decay); kz Ritz vectors returned
+    const int k = o.block_p > 0 ? o.block_p : kz;
     const int64_t mn = n < d ? n : d;
     int q_eff = q;
     bool deflated = false;
@@ -468,7 +470,7 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
             return fail(ctx, BKS_ERR_UNSUPPORTED,
                         "Krylov width " + std::to_string(w) + " exceeds the Jacobi solver's limit");
     }
-    const int kout = triplets ? w : k;   // Ritz triplets returned
+    const int kout = triplets ? w : kz;   // Ritz vectors returned
     Plan p = make_plan(A, k, q_eff, w, sizeof(T), ctx->num_sms, kout);
     bks_status s = ensure_ws(ctx, p.total);
     if (s != BKS_OK) return s;
@@ -514,8 +516,8 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
     // Eigen-solve: only Ubar_k is needed, so by default M = B^T B goes through the
     // tridiagonal top-k solver; the one-sided Jacobi covers Ritz triplets (all w vectors),
     // SI (w = k), widths beyond the tridiagonal kernels and eig_mode 1.
-    const bool use_td = !o.basis_only && !triplets && o.eig_mode != 1 && o.rr_mode != 1 && k < w &&
-                        tridiag_fits<T>(w, k);
+    const bool use_td = !o.basis_only && !triplets && o.eig_mode != 1 && o.rr_mode != 1 && kz < w &&
+                        tridiag_fits<T>(w, kz);
     const bool rr_qr = !use_td && (o.rr_mode == 1 || (o.rr_mode == 0 && w > 512));
     const bool bf16_mode = o.precision == BKS_PREC_BF16;
     const bool refine = bf16_mode && o.refine != 0;
@@ -605,12 +607,12 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
     const int t_rr = prof.begin();
     int eig_path = 0;
     if (o.basis_only) {
-        // Z = first k columns of Q (Sec. 4.1: enough for low-rank approximation)
-        transpose_in<T>(ex, Qt, sizeof(T) == 8 ? BKS_F64 : BKS_F32, k, n, p.ldn, Z, k);
-        row_norms<T>(ex, Bt, k, d, p.ldd, sigma, false);
+        // Z = first kz columns of Q (Sec. 4.1: enough for low-rank approximation)
+        transpose_in<T>(ex, Qt, sizeof(T) == 8 ? BKS_F64 : BKS_F32, kz, n, p.ldn, Z, kz);
+        row_norms<T>(ex, Bt, kz, d, p.ldd, sigma, false);
         if (V != nullptr) {
-            row_norms<T>(ex, Bt, k, d, p.ldd, sigma, true);
-            transpose_in<T>(ex, Bt, sizeof(T) == 8 ? BKS_F64 : BKS_F32, k, d, p.ldd, V, k);
+            row_norms<T>(ex, Bt, kz, d, p.ldd, sigma, true);
+            transpose_in<T>(ex, Bt, sizeof(T) == 8 ? BKS_F64 : BKS_F32, kz, d, p.ldd, V, kz);
         }
     } else {
         // a5: M = B^T B, by default through a triangular factor: with B = Q_B R (block QR
@@ -629,7 +631,7 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
         check_finite<T>(ex, Rm, int64_t(w) * w);
         // a6: eigen-decomposition of M, descending (row j of Rm is column j of R^T)
         const int sweeps = o.jacobi_max_sweeps > 0 ? o.jacobi_max_sweeps : 40;
-        eig_path = use_td && topk_tridiag<T>(ex, w, Rm, k, Vt, w, reinterpret_cast<T*>(base + p.td), ows) ? 1 : 0;
+        eig_path = use_td && topk_tridiag<T>(ex, w, Rm, kz, Vt, w, reinterpret_cast<T*>(base + p.td), ows) ? 1 : 0;
         if (eig_path == 0)
             sym_eig<T>(ex, w, Rm, w, JX, w, lam, nrm, Vt, w, order, sweeps, o.jacobi_tol, stat + 1);
         // a7: Z = Q Ubar_k (row-major n x k)
@@ -728,6 +730,14 @@ bks_status solve_entry(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t
         return fail(ctx, BKS_ERR_UNSUPPORTED, "a CSR matrix is solved on the FP32 path");
     if (triplets && o.basis_only)
         return fail(ctx, BKS_ERR_INVALID_ARG, "Ritz triplets need the Rayleigh-Ritz step (basis_only = 0)");
+    if (o.block_p != 0) {
+        if (o.block_p < k || int64_t(o.block_p) > mn)
+            return fail(ctx, BKS_ERR_INVALID_ARG, "block_p must be 0 or in [k, min(n, d)]");
+        if (o.block_p > 128)
+            return fail(ctx, BKS_ERR_UNSUPPORTED, "block_p > 128: block Cholesky factors are held on one SM");
+        if (triplets && o.block_p != k)
+            return fail(ctx, BKS_ERR_INVALID_ARG, "Ritz triplets are computed with block_p = k");
+    }
     if (defer) o.profile = 0;
     if (prec == BKS_PREC_F64)
         return solve<double>(ctx, A, k, q, seed, pi, Z, sigma, V, o, st, krylov, triplets, defer);
@@ -858,6 +868,9 @@ bks_status bks_workspace_size(const bks_matrix* A, int k, int q, int method, con
     int prec = o.precision;
     if (prec == BKS_PREC_AUTO) prec = A->dtype == BKS_F64 ? BKS_PREC_F64 : BKS_PREC_F32;
     const size_t tb = prec == BKS_PREC_F64 ? 8 : 4;
+    const int kz = k;
+    if (o.block_p != 0 && (o.block_p < kz || int64_t(o.block_p) > mn)) return BKS_ERR_INVALID_ARG;
+    k = o.block_p > 0 ? o.block_p : kz;   // block size
     int q_eff = q;
     if (method == 0) {
         const int64_t cap = mn / k - 1;

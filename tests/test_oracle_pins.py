@@ -65,6 +65,54 @@ def test_block_krylov_exact_when_width_covers_rank():
         assert abs(abs(res.Z[:, i] @ u[:, i]) - 1) < 1e-10
 
 
+# ------------------------------------------- block size p >= k (Sec. 8, spectral decay)
+def test_block_p_exact_when_first_block_covers_rank():
+    # rank 20, k = 5, p = 20, q = 0: span(A Pi) = range(A), so Z = U_5 and sigma exact
+    sig = np.concatenate([1.0 / np.arange(1, 21), np.zeros(20)])
+    a, u, v = _planted(60, 40, sig, 12)
+    pi = synth.gaussian_pi(3, 40, 20, np.float64)
+    for fn in (krylov.block_krylov, krylov.simul_iter):
+        res = fn(a, 5, 0, pi)
+        assert res.Q.shape == (60, 20) and res.Z.shape == (60, 5)
+        assert np.max(np.abs(res.sigma - sig[:5]) / sig[:5]) < 1e-12
+        assert metrics.subspace_distance(res.Z, u[:, :5]) < 1e-10
+
+
+@pytest.mark.parametrize("fn", [krylov.block_krylov, krylov.simul_iter])
+def test_block_p_ritz_values_dominate_block_k(fn):
+    # Pi_p = [Pi_k, more columns]: span(Q_p) contains span(Q_k), so by Courant-Fischer
+    # every one of the k leading Ritz values can only grow
+    a, _ = synth.dense_planted_noisy(n=800, d=500, rank=100, seed=4)
+    pi = synth.gaussian_pi(5, 500, 16, np.float64)
+    for q in (0, 1, 3):
+        rk = fn(a, 8, q, pi[:, :8])
+        rp = fn(a, 8, q, pi)
+        assert np.all(rp.sigma >= rk.sigma - 1e-12 * rk.sigma[0])
+
+
+def test_block_p_gap_dependent_convergence():
+    # Theorem "Gap Dependent Convergence": with sigma_k / sigma_{k+1} - 1 ~ 1e-3 but
+    # sigma_k / sigma_{p+1} = 2, p = 20 reaches the per-vector and spectral guarantees
+    # at q = 2 where p = k = 10 does not
+    sig = np.concatenate([np.linspace(1.0, 0.9, 10), np.linspace(0.899, 0.88, 10),
+                          0.45 * np.exp(-np.arange(380) / 30)])
+    a, u, v = _planted(600, 400, sig, 21)
+    slow = 0
+    for s in range(5):
+        pi = synth.gaussian_pi(30 + s, 400, 20, np.float64)
+        rp = metrics.ratios(a, krylov.block_krylov(a, 10, 2, pi).Z, 10, sigma=sig)
+        rk = metrics.ratios(a, krylov.block_krylov(a, 10, 2, pi[:, :10]).Z, 10, sigma=sig)
+        assert rp["per_vector"] <= 1.001 and rp["spectral"] <= 1.001
+        slow += int(rk["per_vector"] > 1.01)
+    assert slow >= 4
+
+
+def test_block_p_rejects_fewer_than_k_columns():
+    a, _, _ = _planted(30, 20, 1.0 / np.arange(1, 21), 1)
+    with pytest.raises(ValueError):
+        krylov.block_krylov(a, 5, 1, synth.gaussian_pi(1, 20, 4, np.float64))
+
+
 def test_q_capped_when_width_exceeds_dimension():
     a, _, _ = _planted(64, 48, 1.0 / np.arange(1, 49), 5)
     res = krylov.block_krylov(a, 16, 4, synth.gaussian_pi(2, 48, 16))
