@@ -42,6 +42,9 @@ def parse():
     p.add_argument("--method", default="bki", choices=["bki", "si"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--workload", default="dense", choices=["dense", "sparse", "bf16", "batched"])
+    p.add_argument("--block-p", type=int, default=0,
+                   help="p >= k columns in Pi and in every Krylov block (Sec. 8); 0 = k")
+    p.add_argument("--q", type=int, default=None, help="iteration count (default: the workload's)")
     return p.parse_args()
 
 
@@ -259,7 +262,8 @@ class Setup:
     def run(self, seed, stats=False, profile=False):
         if self.batch is not None:
             out = self.bk.block_krylov_batched(self.batch, self.k, self.q,
-                                               seeds=[seed * 1000 + i for i in range(256)], stats=True)
+                                               seeds=[seed * 1000 + i for i in range(256)], stats=True,
+                                               **self.solve_kw)
             return out[1] if stats else out[0]
         r = self.solve(self.a, self.k, self.q, seed=seed, stats=stats, profile=profile, **self.solve_kw)
         return r[2] if stats else r
@@ -270,14 +274,14 @@ class Setup:
         import torch
         if self.name == "dense":
             ad = self.pinned.to(dev, non_blocking=True)
-            z, s = self.solve(ad, self.k, self.q, seed=seed)
+            z, s = self.solve(ad, self.k, self.q, seed=seed, **self.solve_kw)
             zh, sh = z.cpu(), s.cpu()
             return self.host.nbytes, zh.numel() * 4 + sh.numel() * 4
         if self.name == "sparse":
             import paper_1504_05477_gb300 as bk
             parts = [x.to(dev, non_blocking=True) for x in self.pinned]
             a = bk.CsrMatrix(parts[0], parts[1], parts[2], (200000, self.shape["d"]), col_mean=parts[3])
-            z, s = self.solve(a, self.k, self.q, seed=seed)
+            z, s = self.solve(a, self.k, self.q, seed=seed, **self.solve_kw)
             zh, sh = z.cpu(), s.cpu()
             return sum(x.numel() * x.element_size() for x in self.pinned), zh.numel() * 4 + sh.numel() * 4
         if self.name == "bf16":
@@ -286,7 +290,8 @@ class Setup:
             zh, sh = z.cpu(), s.cpu()
             return self.pinned.numel() * 2, zh.numel() * 4 + sh.numel() * 4
         mats = [m.to(dev, non_blocking=True) for m in self.pinned]
-        outs = self.bk.block_krylov_batched(mats, self.k, self.q, seeds=[seed * 1000 + i for i in range(256)])
+        outs = self.bk.block_krylov_batched(mats, self.k, self.q, seeds=[seed * 1000 + i for i in range(256)],
+                                            **self.solve_kw)
         d2h = 0
         for z, s in outs:
             d2h += z.cpu().numel() * 4 + s.cpu().numel() * 4
@@ -356,6 +361,10 @@ def main():
     dev = torch.device("cuda", local)
 
     w = Setup(args.workload, rank, dev, args.method)
+    if args.q is not None:
+        w.q = args.q
+    if args.block_p:
+        w.solve_kw["block_p"] = args.block_p
 
     def barrier():
         if world > 1:
@@ -393,7 +402,7 @@ def main():
         # algorithmic bytes of one product: A once, the thin operand and the result (the
         # BF16 refinement's wider product is left out: the kernel log times the others)
         if w.name == "bf16":
-            bytes_per_product = 65536 * 16384 * 2 + w.k * (65536 + 16384) * 4
+            bytes_per_product = 65536 * 16384 * 2 + (w.solve_kw.get("block_p") or w.k) * (65536 + 16384) * 4
         else:
             bytes_per_product = st["product_bytes"] / nprod
         if klaunch > 0:   # the dominant kernel alone, timed by events around each launch
@@ -442,10 +451,13 @@ def main():
             torch.distributed.destroy_process_group()
         return
     cpu = None
-    if not args.no_cpu_baseline and world == 1 and w.cpu is not None:
+    overridden = args.q is not None or args.block_p   # the CPU sample times the default workload
+    if not args.no_cpu_baseline and world == 1 and w.cpu is not None and not overridden:
         cpu = w.cpu()
     config = {"workload": w.desc, "method": "block_krylov" if args.method == "bki" else "simul_iter",
               "k": w.k, "q": w.q, "width": width, "parallelism": f"replicas x{world}", "l2": w.l2}
+    if args.block_p:
+        config["block_p"] = args.block_p
     config.update(w.shape)
     line = {
         "metric": METRIC, "value": value, "unit": "ms per solve", "n_gpus": world,
