@@ -354,9 +354,16 @@ Plan make_plan(const bks_matrix* A, int k, int q_eff, int w, size_t tb, int sms,
         p.td = a.take(fits ? tridiag_scratch_elems(w, kout) * tb : 0);
     }
     const int64_t ldmax = p.ldn > p.ldd ? p.ldn : p.ldd;
-    p.xh = a.take(size_t(k) * ldmax * 4);
-    p.xl = a.take(size_t(k) * ldmax * 4);
+    // hi/lo split of a thin operand: a k-wide block, or (FP32) all w rows of B for M = B^T B
+    size_t xcap = size_t(k) * ldmax;
+    if (tb == 4 && size_t(w) * p.ldd > xcap) xcap = size_t(w) * p.ldd;
+    p.xh = a.take(xcap * 4);
+    p.xl = a.take(xcap * 4);
     p.tpart_cap = tc_partial_floats(n, d, k, sms);
+    if (tb == 4) {
+        const int64_t b = tc_partial_floats(w, d, w, sms);   // M = B^T B on the tensor cores
+        if (b > p.tpart_cap) p.tpart_cap = b;
+    }
     if (on.tcap > p.tpart_cap) p.tpart_cap = on.tcap;
     if (od.tcap > p.tpart_cap) p.tpart_cap = od.tcap;
     (void)ldmax0;
@@ -627,7 +634,16 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
         gm.X = rr_qr ? QBt : Bt; gm.ldx = p.ldd; gm.Y = Bt; gm.ldy = p.ldd;
         gm.y_kmajor = true; gm.y_dtype = sizeof(T) == 8 ? BKS_F64 : BKS_F32;
         gm.out = Rm; gm.ldo = w; gm.alpha = 1.0; gm.beta = 0.0;
-        gemm_simt<T>(ex, gm, part, p.part_cap);
+        // FP32: on the tensor cores (3xTF32): row j of Rm = row j of (A X)^T with A = B and
+        // X = B (M, symmetric) or X = Q_B (row j of R = Q_B^T B)
+        KernelLog* klog = ex.klog;   // the kernel log times products with A only
+        ex.klog = nullptr;
+        const bool tc_m = sizeof(T) == 4 && o.product_path != 1 &&
+                          tc_product_f32(ex, reinterpret_cast<const float*>(Bt), w, d, p.ldd, false, w,
+                                         reinterpret_cast<const float*>(rr_qr ? QBt : Bt), p.ldd,
+                                         reinterpret_cast<float*>(Rm), w, pw.xh, pw.xl, pw.tpart, pw.tpart_cap);
+        ex.klog = klog;
+        if (!tc_m) gemm_simt<T>(ex, gm, part, p.part_cap);
         check_finite<T>(ex, Rm, int64_t(w) * w);
         // a6: eigen-decomposition of M, descending (row j of Rm is column j of R^T)
         const int sweeps = o.jacobi_max_sweeps > 0 ? o.jacobi_max_sweeps : 40;

@@ -116,6 +116,30 @@ def zipf_idf_csr(n=200000, d=60000, per_row=50, s=1.1, seed=1003):
     return row_ptr, cols.ravel().astype(np.int32), vals.ravel().astype(np.float32), d
 
 
+def powerlaw_graph_csr(n=262144, out_a=2.0, max_out=2000, s_in=0.9, seed=1006):
+    """Directed graph adjacency as a square binary CSR (the stand-in for the paper's
+    SNAP/amazon0302 shape class: 262111 nodes, 1.23e6 edges, power-law degrees).
+
+    Out-degree of node u ~ Zipf(out_a) clipped to [1, max_out]; its targets are drawn
+    by inverse CDF from Zipf(s_in) over node ranks, mapped through a seeded permutation
+    (so the hubs are spread over the index range); repeated targets and self loops are
+    dropped; indices sorted within each row; every value is 1.
+    Returns (row_ptr int64[n+1], col_idx int32[nnz], vals float32[nnz], n).
+    """
+    rng = np.random.default_rng(seed)
+    deg = np.minimum(rng.zipf(out_a, size=n), max_out).astype(np.int64)
+    perm = rng.permutation(n).astype(np.int64)
+    cdf = _zipf_cdf(n, s_in)
+    src = np.repeat(np.arange(n, dtype=np.int64), deg)
+    dst = perm[np.minimum(np.searchsorted(cdf, rng.random(src.size), side="right"), n - 1)]
+    keep = dst != src
+    key = np.unique(src[keep] * n + dst[keep])   # sorted by (row, column), duplicates gone
+    rows, cols = key // n, key % n
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=n), out=row_ptr[1:])
+    return row_ptr, cols.astype(np.int32), np.ones(cols.size, dtype=np.float32), n
+
+
 def column_means(row_ptr, col_idx, vals, n, d) -> np.ndarray:
     """mu_j = (1/n) sum_i A_ij: the column means used for implicit centring (FP32)."""
     s = np.bincount(col_idx, weights=vals.astype(np.float64), minlength=d)

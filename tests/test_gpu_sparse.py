@@ -175,3 +175,21 @@ def test_sparse_invalid_structure_is_rejected(defect):
                    np.array([2.0, 3.0], np.float32), 2, 2)
     y = host(bk.matmul(good, dev(np.eye(2, dtype=np.float32))))
     assert np.array_equal(y, np.array([[0, 2], [3, 0]], np.float32))
+
+
+@pytest.mark.parametrize("method", ["bki", "si"])
+def test_graph_adjacency_centred_parity(method):
+    """Square power-law adjacency (the graph workload's shape class), column-centred as
+    the paper's principal components, k = 10, q = 6, against the oracle."""
+    n, k, q = 6000, 10, 6
+    row_ptr, col_idx, vals, n = synth.powerlaw_graph_csr(n=n, seed=8)
+    mu = synth.column_means(row_ptr, col_idx, vals, n, n)
+    a = gpu_csr(row_ptr, col_idx, vals, n, n, mu)
+    pi = synth.gaussian_pi(4, n, k)
+    fn = bk.block_krylov if method == "bki" else bk.simul_iter
+    z, s = fn(a, k, q, pi=dev(pi))
+    z, s = host(z).astype(np.float64), host(s).astype(np.float64)
+    op = krylov.centred_csr_op(row_ptr, col_idx, vals, n, n, mu)
+    ref = (krylov.block_krylov if method == "bki" else krylov.simul_iter)(op, k, q, pi)
+    assert np.max(np.abs(s - ref.sigma) / ref.sigma) <= 1e-5
+    assert np.max(np.abs(z.T @ z - np.eye(k))) < 1e-4
