@@ -45,6 +45,9 @@ def parse():
     p.add_argument("--block-p", type=int, default=0,
                    help="p >= k columns in Pi and in every Krylov block (Sec. 8); 0 = k")
     p.add_argument("--q", type=int, default=None, help="iteration count (default: the workload's)")
+    p.add_argument("--adapt-tol", type=float, default=0.0,
+                   help="Block Krylov with q chosen on the fly (at most q): stop once no leading Ritz "
+                        "value moves by more than this (relative) between iterations")
     return p.parse_args()
 
 
@@ -385,6 +388,10 @@ def main():
         w.q = args.q
     if args.block_p:
         w.solve_kw["block_p"] = args.block_p
+    if args.adapt_tol > 0:
+        import paper_1504_05477_gb300 as bk
+        tol = args.adapt_tol
+        w.solve = lambda a, k, q, **kw: bk.block_krylov_adaptive(a, k, q, tol, **kw)
 
     def barrier():
         if world > 1:
@@ -430,6 +437,7 @@ def main():
     if w.batch is None:
         # per-kernel-class event times of profiled solves (same launch configuration)
         st = w.run(7, stats=True, profile=True)
+        nprod = 2 * st["q_eff"] + 2   # products of one solve (the adaptive count may be lower)
         prof_runs = [w.run(8 + i, stats=True, profile=True) for i in range(3)]
         ms_prod = statistics.median(r["ms_product"] for r in prof_runs)
         klaunch = prof_runs[0]["product_kernel_launches"]
@@ -485,13 +493,17 @@ def main():
             torch.distributed.destroy_process_group()
         return
     cpu = None
-    overridden = args.q is not None or args.block_p   # the CPU sample times the default workload
+    overridden = args.q is not None or args.block_p or args.adapt_tol > 0   # the CPU sample times the default workload
     if not args.no_cpu_baseline and world == 1 and w.cpu is not None and not overridden:
         cpu = w.cpu()
     config = {"workload": w.desc, "method": "block_krylov" if args.method == "bki" else "simul_iter",
               "k": w.k, "q": w.q, "width": width, "parallelism": f"replicas x{world}", "l2": w.l2}
     if args.block_p:
         config["block_p"] = args.block_p
+    if args.adapt_tol > 0:
+        config["adapt_tol"] = args.adapt_tol
+        config["q"] = f"adaptive, at most {w.q}"
+        config["q_run"] = st["q_eff"]
     config.update(w.shape)
     line = {
         "metric": METRIC, "value": value, "unit": "ms per solve", "n_gpus": world,

@@ -179,6 +179,21 @@ bks_status bks_simul_iter(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint6
                           const void* pi, void* Z, void* sigma, void* V,
                           const bks_opts* opts, bks_stats* stats);
 
+/* Block Krylov Iteration with the iteration count chosen on the fly (extends the q of
+ * Algorithm 2; Sec. 8 bounds q through sigma_k / sigma_{p+1}, which a caller rarely
+ * knows).  After B_{i-1} = A^T Q_{i-1} (which the next block needs anyway) the k leading
+ * Ritz values of the i-block space are computed (M_i = B^T B over those blocks,
+ * tridiagonal form and bisection, no vectors); the iteration stops at the first i >= 2
+ * where every one of them moved by at most `tol` (relative) since i - 1 blocks, and the
+ * Rayleigh-Ritz step runs on those i blocks.  Otherwise it runs q_max iterations
+ * (capped as in bks_block_krylov).  stats->q_eff reports the iterations run.  The test
+ * reads k values back to the host once per iteration (a stream synchronisation).
+ * tol in (0, 1); other arguments as bks_block_krylov (opts.block_p applies).  With
+ * widths beyond the tridiagonal kernels the test is skipped and q_max iterations run. */
+bks_status bks_block_krylov_adaptive(bks_ctx* ctx, const bks_matrix* A, int k, int q_max, double tol,
+                                     uint64_t seed, const void* pi, void* Z, void* sigma, void* V,
+                                     const bks_opts* opts, bks_stats* stats);
+
 /* ---- building blocks (each one step of the path, exposed for tests and timing) ------ */
 
 /* Start block Pi (Alg. 1/2 step 1), d x k row-major, generated on the device:

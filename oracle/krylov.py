@@ -162,6 +162,46 @@ def block_krylov(a, k: int, q: int, pi) -> Result:
     return _rayleigh_ritz(np.hstack(qs), np.hstack(bs), k, q_eff)
 
 
+def ritz_values(b_mat: np.ndarray, k: int) -> np.ndarray:
+    """The min(k, w) leading Ritz values sqrt(lambda_i(B^T B)) of the space whose kept
+    products are the columns of B (Lemma 4.1: M = B^T B)."""
+    lam = np.linalg.eigvalsh(b_mat.T @ b_mat)[::-1]
+    return np.sqrt(np.maximum(lam[:min(k, lam.size)], 0.0))
+
+
+def block_krylov_adaptive(a, k: int, q_max: int, tol: float, pi):
+    """Algorithm 2 with the iteration count chosen on the fly.  After B_{i-1} = A^T Q_{i-1}
+    the k leading Ritz values of the i-block space are compared with those of the
+    (i-1)-block space; the first i >= 2 where none moved by more than tol (relative to its
+    new value) ends the iteration, and Rayleigh-Ritz runs on those i blocks (q = i - 1).
+    Returns (Result, the relative changes observed, in order)."""
+    op = _as_op(a)
+    pi64 = _start_block(pi, op.d, k)
+    q_cap = q_effective(op.n, op.d, pi64.shape[1], q_max)
+    qs = [orthonormalise(op.mul(pi64))]
+    bs = []
+    prev = None
+    deltas = []
+    for i in range(1, q_cap + 1):
+        b_prev = op.tmul(qs[-1])
+        bs.append(b_prev)
+        cur = ritz_values(np.hstack(bs), k)
+        if prev is not None:
+            floor = 1e-30 + 1e-12 * cur[0]
+            delta = float(np.max(np.abs(cur - prev) / np.maximum(cur, floor)))
+            deltas.append(delta)
+            if delta <= tol:
+                return _rayleigh_ritz(np.hstack(qs), np.hstack(bs), k, i - 1), deltas
+        prev = cur
+        w = op.mul(b_prev)
+        q_cat = np.hstack(qs)
+        for _pass in range(2):
+            w = w - q_cat @ (q_cat.T @ w)
+        qs.append(orthonormalise(w))
+    bs.append(op.tmul(qs[-1]))
+    return _rayleigh_ritz(np.hstack(qs), np.hstack(bs), k, q_cap), deltas
+
+
 def simul_iter(a, k: int, q: int, pi) -> Result:
     """Algorithm 1 (Simultaneous Iteration), FP64, orthonormalised after every
     iteration (Sec. 4.1): Q <- orth(A A^T Q), starting from Q = orth(A Pi)."""

@@ -14,7 +14,7 @@ import ctypes
 from . import _binding as B
 from ._binding import BksError, BksMatrix, BksOpts, BksStats  # noqa: F401
 
-__all__ = ["block_krylov", "simul_iter", "matmul", "orthonormalize", "sym_eig", "gen_pi", "CsrMatrix",
+__all__ = ["block_krylov", "block_krylov_adaptive", "simul_iter", "matmul", "orthonormalize", "sym_eig", "gen_pi", "CsrMatrix",
            "ritz_triplets", "low_rank", "backward", "rand_svd", "krylov_width", "block_krylov_batched",
            "gen_pi_host", "Context", "context", "dense_matrix", "BksError", "lib_path"]
 
@@ -177,7 +177,7 @@ def _out_dtype(a, precision):
     return torch.float32
 
 
-def _solve(fn_name, a, k, q, seed, pi, want_v, precision, stats, **kw):
+def _solve(fn_name, a, k, q, seed, pi, want_v, precision, stats, _tol=None, **kw):
     torch = _torch()
     mat, dev, odt = _as_bks(a, precision)
     ctx = context(dev)
@@ -192,7 +192,10 @@ def _solve(fn_name, a, k, q, seed, pi, want_v, precision, stats, **kw):
     opts = _opts(precision=precision, **kw)
     st = BksStats()
     fn = getattr(ctx.lib, fn_name)
-    status = fn(ctx.ptr, ctypes.byref(mat), int(k), int(q), ctypes.c_uint64(seed & (2**64 - 1)),
+    head = (ctx.ptr, ctypes.byref(mat), int(k), int(q))
+    if _tol is not None:
+        head = head + (ctypes.c_double(_tol),)
+    status = fn(*head, ctypes.c_uint64(seed & (2**64 - 1)),
                 ctypes.c_void_p(pi.data_ptr()) if pi is not None else None,
                 ctypes.c_void_p(z.data_ptr()), ctypes.c_void_p(sig.data_ptr()),
                 ctypes.c_void_p(v.data_ptr()) if v is not None else None,
@@ -208,6 +211,14 @@ def block_krylov(a, k, q, seed=0, pi=None, want_v=False, precision="auto", stats
     want_v also V (d x k); with stats also a dict of bks_stats.  block_p = p > k runs the
     iteration with p columns in Pi and in every block (Sec. 8); pi is then d x p."""
     return _solve("bks_block_krylov", a, k, q, seed, pi, want_v, precision, stats, **kw)
+
+
+def block_krylov_adaptive(a, k, q_max, tol, seed=0, pi=None, want_v=False, precision="auto", stats=False, **kw):
+    """Algorithm 2 with q chosen on the fly (bks_block_krylov_adaptive): stops once none of
+    the k leading Ritz values moves by more than tol (relative) between iterations, at most
+    q_max iterations; stats["q_eff"] reports the iterations run."""
+    return _solve("bks_block_krylov_adaptive", a, k, q_max, seed, pi, want_v, precision, stats,
+                  _tol=float(tol), **kw)
 
 
 def simul_iter(a, k, q, seed=0, pi=None, want_v=False, precision="auto", stats=False, **kw):

@@ -69,6 +69,8 @@ SIGNATURES = {
     "bks_version": (_I32, []),
     "bks_block_krylov": (_I32, [_P, ctypes.POINTER(BksMatrix), _I32, _I32, _U64, _P, _P, _P, _P,
                                 ctypes.POINTER(BksOpts), ctypes.POINTER(BksStats)]),
+    "bks_block_krylov_adaptive": (_I32, [_P, ctypes.POINTER(BksMatrix), _I32, _I32, ctypes.c_double, _U64, _P,
+                                         _P, _P, _P, ctypes.POINTER(BksOpts), ctypes.POINTER(BksStats)]),
     "bks_simul_iter": (_I32, [_P, ctypes.POINTER(BksMatrix), _I32, _I32, _U64, _P, _P, _P, _P,
                               ctypes.POINTER(BksOpts), ctypes.POINTER(BksStats)]),
     "bks_gen_pi": (_I32, [_P, _U64, _I64, _I32, _I32, _P]),

@@ -195,6 +195,11 @@ size_t tridiag_scratch_elems(int w, int m);
 struct OrthWs;
 template <typename T>
 bool topk_tridiag(Exec& ex, int w, const T* M, int m, T* Vt, int64_t ldv, T* scratch, const OrthWs& ows);
+// The m largest eigenvalues alone (tridiagonal form and multisection): on return *lam
+// points at m device values, descending, to be multiplied by the device scalar at
+// *scale; both live in `scratch`.
+template <typename T>
+bool topk_values(Exec& ex, int w, const T* M, int m, T* scratch, const T** lam, const T** scale);
 
 // Column-wise argmax |.| sign normalisation of a row-major n x k matrix (and the
 // matching rows of Ut, k x ldu).

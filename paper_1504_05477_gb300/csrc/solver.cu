@@ -8,6 +8,7 @@
 //   Z = Q Ubar_k;  sigma_i = |B ubar_i| (= |A^T z_i|, the Ritz values).
 // Simultaneous Iteration (Alg. 1): Q <- orth(A (A^T Q)) q times, then the same
 // Rayleigh-Ritz step with w = k (Sec. 4.1).
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -41,6 +42,7 @@ struct bks_ctx {
     size_t ws_bytes = 0;
     bool ws_owned = false;
     int* host_status = nullptr;   // pinned: [status, sweeps, shifted]
+    double* host_vals = nullptr;  // pinned, 256 doubles: Ritz values of the adaptive stopping test
     std::string last_error;
     std::vector<cudaEvent_t> events;
     KernelLog klog;
@@ -287,7 +289,7 @@ struct Plan {
     int64_t tpart_cap, xb_cap;
     bool sparse;
     CsrLayout csr;
-    size_t td;               // scratch of the tridiagonal eigen-solve (0 bytes when it cannot run)
+    size_t td, td_bytes;     // scratch of the tridiagonal eigen-solve (0 bytes when it cannot run)
     size_t Qt, Bt, QBt, Pit, W, Wtmp, Wb, Wbtmp, part, og, rfac, ct, Rm, JX, lam, nrm, Vt,
         order, Vk, stat, fpart, fgram, fbar;
     int64_t fcap;
@@ -351,7 +353,8 @@ Plan make_plan(const bks_matrix* A, int k, int q_eff, int w, size_t tb, int sms,
     p.Vk = a.take(size_t(kout) * p.ldd * tb);
     {
         const bool fits = tb == 4 ? tridiag_fits<float>(w, kout) : tridiag_fits<double>(w, kout);
-        p.td = a.take(fits ? tridiag_scratch_elems(w, kout) * tb : 0);
+        p.td_bytes = fits ? tridiag_scratch_elems(w, kout) * tb : 0;
+        p.td = a.take(p.td_bytes);
     }
     const int64_t ldmax = p.ldn > p.ldd ? p.ldn : p.ldd;
     // hi/lo split of a thin operand: a k-wide block, or (FP32) all w rows of B for M = B^T B
@@ -458,7 +461,7 @@ bks_status finish_solve(bks_ctx* ctx, bks_stats* st) {
 template <typename T>
 bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed, const void* pi,
                  void* Zv, void* sigv, void* Vv, const bks_opts& o, bks_stats* st, bool krylov,
-                 bool triplets, bool defer) {
+                 bool triplets, bool defer, double adapt_tol) {
     const int64_t n = A->n, d = A->d;
     // block size: the p >= kz columns of Pi (Sec. 8, spectral decay); kz Ritz vectors returned
     const int k = o.block_p > 0 ? o.block_p : kz;
@@ -585,13 +588,76 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
         prof.end(1, b);
     };
 
+    // Adaptive q: after B_{i-1} = A^T Q_{i-1}, the kz leading Ritz values of the i-block space
+    // (M_i = B^T B over those blocks, tridiagonal form and multisection only); the
+    // iteration stops at the first i >= 2 where none moved by more than adapt_tol
+    // (relative) since i - 1 blocks.  B_{i-1} is then the last kept block: no product is
+    // spent on the test.
+    const bool adaptive = krylov && adapt_tol > 0 && !o.basis_only && p.td_bytes > 0;
+    std::vector<double> prev_vals;
+    auto stagnated = [&](int nb) -> bool {
+        const int wc = nb * k;
+        KernelLog* klog = ex.klog;
+        ex.klog = nullptr;
+        const bool tc = sizeof(T) == 4 && o.product_path != 1 &&
+                        tc_product_f32(ex, reinterpret_cast<const float*>(Bt), wc, d, p.ldd, false, wc,
+                                       reinterpret_cast<const float*>(Bt), p.ldd, reinterpret_cast<float*>(Rm),
+                                       wc, pw.xh, pw.xl, pw.tpart, pw.tpart_cap);
+        ex.klog = klog;
+        if (!tc) {
+            GemmDesc g{};
+            g.M = wc; g.N = wc; g.K = d;
+            g.X = Bt; g.ldx = p.ldd; g.Y = Bt; g.ldy = p.ldd;
+            g.y_kmajor = true; g.y_dtype = sizeof(T) == 8 ? BKS_F64 : BKS_F32;
+            g.out = Rm; g.ldo = wc; g.alpha = 1.0; g.beta = 0.0;
+            gemm_simt<T>(ex, g, part, p.part_cap);
+        }
+        const int m = kz < wc ? kz : wc;
+        const T* lam_d = nullptr;
+        const T* scale_d = nullptr;
+        if (!topk_values<T>(ex, wc, Rm, m, reinterpret_cast<T*>(base + p.td), &lam_d, &scale_d)) return false;
+        if (ctx->host_vals == nullptr && cudaMallocHost(&ctx->host_vals, 256 * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->host_vals = nullptr;
+            return false;
+        }
+        T* hv = reinterpret_cast<T*>(ctx->host_vals);
+        cudaMemcpyAsync(hv, lam_d, size_t(m) * sizeof(T), cudaMemcpyDeviceToHost, ex.stream);
+        cudaMemcpyAsync(hv + m, scale_d, sizeof(T), cudaMemcpyDeviceToHost, ex.stream);
+        if (cudaStreamSynchronize(ex.stream) != cudaSuccess) return false;
+        std::vector<double> cur(m);
+        for (int j = 0; j < m; ++j) {
+            const double l = double(hv[j]) * double(hv[m]);
+            cur[j] = l > 0 ? std::sqrt(l) : 0.0;
+        }
+        bool done = false;
+        if (prev_vals.size() == size_t(m)) {
+            double delta = 0;
+            const double floor = 1e-30 + 1e-12 * cur[0];
+            for (int j = 0; j < m; ++j) {
+                const double dj = std::fabs(cur[j] - prev_vals[j]) / (cur[j] > floor ? cur[j] : floor);
+                if (!(dj <= delta)) delta = dj;   // NaN counts as not converged
+            }
+            done = delta <= adapt_tol;
+        }
+        prev_vals.swap(cur);
+        return done;
+    };
+
     // a1 + a4: W_0 = A Pi, Q_0 = orth(W_0)
     prod(false, Pit, p.ldd, W, p.ldn, k);
     orth(0, Qt);
+    int q_run = q_eff;   // iterations run (fewer when the adaptive test stops early)
+    bool stopped = false;
     for (int i = 1; i <= q_eff; ++i) {
         T* Qprev = krylov ? Qt + size_t(i - 1) * k * p.ldn : Qt;
         T* Bprev = krylov ? Bt + size_t(i - 1) * k * p.ldd : Bt;
         prod(true, Qprev, p.ldn, Bprev, p.ldd, k);       // a2: B_{i-1} = A^T Q_{i-1}
+        if (adaptive && stagnated(i) && i >= 2) {
+            q_run = i - 1;
+            stopped = true;
+            break;
+        }
         if (krylov && !o.basis_only && !refine && rr_qr) orth_b((i - 1) * k, Bprev);
         prod(false, Bprev, p.ldd, W, p.ldn, k);           // a3: W_i = A B_{i-1}
         if (krylov)
@@ -599,16 +665,17 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
         else
             orth(0, Qt);                                  // a9: SI re-orthonormalisation
     }
-    T* Blast = krylov ? Bt + size_t(q_eff) * k * p.ldd : Bt;
-    const T* Qlast = krylov ? Qt + size_t(q_eff) * k * p.ldn : Qt;
+    const int wr = krylov ? k * (q_run + 1) : k;   // width of the space Rayleigh-Ritz works on
+    T* Blast = krylov ? Bt + size_t(q_run) * k * p.ldd : Bt;
+    const T* Qlast = krylov ? Qt + size_t(q_run) * k * p.ldn : Qt;
     if (!refine) {
-        prod(true, Qlast, p.ldn, Blast, p.ldd, k);        // a5: B_q = A^T Q_q
+        if (!stopped) prod(true, Qlast, p.ldn, Blast, p.ldd, k);   // a5: B_q = A^T Q_q
     } else {
         // a8: B = A^T Q at the full width, FP32-accurate (three BF16 pieces of Q)
         pw.bf16_pieces = 3;
-        prod(true, Qt, p.ldn, Bt, p.ldd, w);
+        prod(true, Qt, p.ldn, Bt, p.ldd, wr);
         if (krylov && !o.basis_only && rr_qr)
-            for (int i = 0; i < q_eff; ++i) orth_b(i * k, Bt + size_t(i) * k * p.ldd);
+            for (int i = 0; i < q_run; ++i) orth_b(i * k, Bt + size_t(i) * k * p.ldd);
     }
 
     const int t_rr = prof.begin();
@@ -622,46 +689,45 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
             transpose_in<T>(ex, Bt, sizeof(T) == 8 ? BKS_F64 : BKS_F32, kz, d, p.ldd, V, kz);
         }
     } else {
-        // a5: M = B^T B, by default through a triangular factor: with B = Q_B R (block QR
-        // of the kept blocks), M = R^T R, R = Q_B^T B.  One-sided Jacobi on R^T converges
-        // to U Sigma with U the eigenvectors of M, in fewer sweeps than on M itself and
-        // without accumulating V (Drmac & Veselic's preconditioned Jacobi SVD).  With
-        // rr_mode 2 the Jacobi runs on M = B^T B directly (columns converge to U Lambda);
-        // only the order of the column norms is used, so both give the same U.
-        if (rr_qr) orth_b(krylov ? q_eff * k : 0, Blast);
+        // a5: M = B^T B.  For the Jacobi at w > 512 (or rr_mode 1) through a triangular
+        // factor instead: with B = Q_B R (block QR of the kept blocks), M = R^T R, R = Q_B^T B,
+        // and one-sided Jacobi on R^T converges to U Sigma with U the eigenvectors of M, in
+        // fewer sweeps than on M itself and without accumulating V (Drmac & Veselic's
+        // preconditioned Jacobi SVD).  Only the order of the column norms is used.
+        if (rr_qr) orth_b(krylov ? q_run * k : 0, Blast);
         GemmDesc gm{};
-        gm.M = w; gm.N = w; gm.K = d;
+        gm.M = wr; gm.N = wr; gm.K = d;
         gm.X = rr_qr ? QBt : Bt; gm.ldx = p.ldd; gm.Y = Bt; gm.ldy = p.ldd;
         gm.y_kmajor = true; gm.y_dtype = sizeof(T) == 8 ? BKS_F64 : BKS_F32;
-        gm.out = Rm; gm.ldo = w; gm.alpha = 1.0; gm.beta = 0.0;
+        gm.out = Rm; gm.ldo = wr; gm.alpha = 1.0; gm.beta = 0.0;
         // FP32: on the tensor cores (3xTF32): row j of Rm = row j of (A X)^T with A = B and
         // X = B (M, symmetric) or X = Q_B (row j of R = Q_B^T B)
         KernelLog* klog = ex.klog;   // the kernel log times products with A only
         ex.klog = nullptr;
         const bool tc_m = sizeof(T) == 4 && o.product_path != 1 &&
-                          tc_product_f32(ex, reinterpret_cast<const float*>(Bt), w, d, p.ldd, false, w,
+                          tc_product_f32(ex, reinterpret_cast<const float*>(Bt), wr, d, p.ldd, false, wr,
                                          reinterpret_cast<const float*>(rr_qr ? QBt : Bt), p.ldd,
-                                         reinterpret_cast<float*>(Rm), w, pw.xh, pw.xl, pw.tpart, pw.tpart_cap);
+                                         reinterpret_cast<float*>(Rm), wr, pw.xh, pw.xl, pw.tpart, pw.tpart_cap);
         ex.klog = klog;
         if (!tc_m) gemm_simt<T>(ex, gm, part, p.part_cap);
-        check_finite<T>(ex, Rm, int64_t(w) * w);
+        check_finite<T>(ex, Rm, int64_t(wr) * wr);
         // a6: eigen-decomposition of M, descending (row j of Rm is column j of R^T)
         const int sweeps = o.jacobi_max_sweeps > 0 ? o.jacobi_max_sweeps : 40;
-        eig_path = use_td && topk_tridiag<T>(ex, w, Rm, kz, Vt, w, reinterpret_cast<T*>(base + p.td), ows) ? 1 : 0;
+        eig_path = use_td && tridiag_fits<T>(wr, kz) && topk_tridiag<T>(ex, wr, Rm, kz, Vt, wr, reinterpret_cast<T*>(base + p.td), ows) ? 1 : 0;
         if (eig_path == 0)
-            sym_eig<T>(ex, w, Rm, w, JX, w, lam, nrm, Vt, w, order, sweeps, o.jacobi_tol, stat + 1);
+            sym_eig<T>(ex, wr, Rm, wr, JX, wr, lam, nrm, Vt, wr, order, sweeps, o.jacobi_tol, stat + 1);
         // a7: Z = Q Ubar_k (row-major n x k)
         GemmDesc gz{};
-        gz.M = kout; gz.N = n; gz.K = w;
-        gz.X = Vt; gz.ldx = w; gz.Y = Qt; gz.ldy = p.ldn;
+        gz.M = kout; gz.N = n; gz.K = wr;
+        gz.X = Vt; gz.ldx = wr; gz.Y = Qt; gz.ldy = p.ldn;
         gz.y_kmajor = false; gz.y_dtype = gm.y_dtype;
         gz.out = Z; gz.ldo = kout; gz.out_transposed = true; gz.alpha = 1.0; gz.beta = 0.0;
         gemm_simt<T>(ex, gz, part, p.part_cap);
-        if (o.sign_fix) sign_fix<T>(ex, Z, n, kout, kout, Vt, w, w);
+        if (o.sign_fix) sign_fix<T>(ex, Z, n, kout, kout, Vt, wr, wr);
         // sigma_i = |B ubar_i| = |A^T z_i|; V_k = B Ubar_k Sigma^{-1}
         GemmDesc gv{};
-        gv.M = kout; gv.N = d; gv.K = w;
-        gv.X = Vt; gv.ldx = w; gv.Y = Bt; gv.ldy = p.ldd;
+        gv.M = kout; gv.N = d; gv.K = wr;
+        gv.X = Vt; gv.ldx = wr; gv.Y = Bt; gv.ldy = p.ldd;
         gv.y_kmajor = false; gv.y_dtype = gm.y_dtype;
         gv.out = Vk; gv.ldo = p.ldd; gv.alpha = 1.0; gv.beta = 0.0;
         gemm_simt<T>(ex, gv, part, p.part_cap);
@@ -677,15 +743,15 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
     if (e != cudaSuccess) return cuda_fail(ctx, e, "solve");
     PendingSolve ps;
     ps.active = true;
-    ps.q_eff = q_eff;
-    ps.w = w;
+    ps.q_eff = q_run;
+    ps.w = wr;
     ps.deflated = deflated;
     ps.basis_only = o.basis_only != 0;
     ps.launches = ex.launches;
     ps.eig_path = eig_path;
     ps.product_launches = ex.product_launches;
     {
-        const int nprod = 2 * q_eff + 2;   // q+1 products with A, q+1 with A^T (both methods)
+        const int nprod = 2 * q_run + 2;   // q+1 products with A, q+1 with A^T (both methods)
         // A once per product (CSR: values + column indices, and the row offsets of A or of
         // A^T, averaged), the thin input read once and the thin output written once.
         const double abytes = A->kind == BKS_CSR
@@ -695,9 +761,9 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
         ps.product_bytes = nprod * (abytes + double(k) * (n + d) * sizeof(T));
         ps.product_flops = nprod * 2.0 * k * nnz_like;
         if (refine) {   // the last A^T product runs at width w (groups of 128 columns)
-            const double groups = double((w + 127) / 128);
-            ps.product_bytes += groups * abytes + double(w - k) * (n + d) * sizeof(T);
-            ps.product_flops += 2.0 * (w - k) * nnz_like;
+            const double groups = double((wr + 127) / 128);
+            ps.product_bytes += groups * abytes + double(wr - k) * (n + d) * sizeof(T);
+            ps.product_flops += 2.0 * (wr - k) * nnz_like;
         }
     }
     ctx->pending = ps;
@@ -722,7 +788,8 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
 
 bks_status solve_entry(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
                        const void* pi, void* Z, void* sigma, void* V, const bks_opts* opts,
-                       bks_stats* st, bool krylov, bool triplets = false, bool defer = false) {
+                       bks_stats* st, bool krylov, bool triplets = false, bool defer = false,
+                       double adapt_tol = 0.0) {
     if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
     bks_status s = check_matrix(ctx, A);
     if (s != BKS_OK) return s;
@@ -756,9 +823,9 @@ bks_status solve_entry(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t
     }
     if (defer) o.profile = 0;
     if (prec == BKS_PREC_F64)
-        return solve<double>(ctx, A, k, q, seed, pi, Z, sigma, V, o, st, krylov, triplets, defer);
+        return solve<double>(ctx, A, k, q, seed, pi, Z, sigma, V, o, st, krylov, triplets, defer, adapt_tol);
     // BF16 and F32 both run the FP32 pipeline (Krylov blocks, Z, sigma in FP32)
-    return solve<float>(ctx, A, k, q, seed, pi, Z, sigma, V, o, st, krylov, triplets, defer);
+    return solve<float>(ctx, A, k, q, seed, pi, Z, sigma, V, o, st, krylov, triplets, defer, adapt_tol);
 }
 
 }  // namespace
@@ -849,6 +916,7 @@ bks_status bks_destroy(bks_ctx* ctx) {
     if (ctx->ws_owned && ctx->ws) cudaFree(ctx->ws);
     for (auto e : ctx->events) cudaEventDestroy(e);
     if (ctx->host_status) cudaFreeHost(ctx->host_status);
+    if (ctx->host_vals) cudaFreeHost(ctx->host_vals);
     delete ctx;
     return BKS_OK;
 }
@@ -906,6 +974,15 @@ bks_status bks_block_krylov(bks_ctx* ctx, const bks_matrix* A, int k, int q, uin
                             const void* pi, void* Z, void* sigma, void* V, const bks_opts* opts,
                             bks_stats* stats) {
     return solve_entry(ctx, A, k, q, seed, pi, Z, sigma, V, opts, stats, true);
+}
+
+bks_status bks_block_krylov_adaptive(bks_ctx* ctx, const bks_matrix* A, int k, int q_max, double tol,
+                                     uint64_t seed, const void* pi, void* Z, void* sigma, void* V,
+                                     const bks_opts* opts, bks_stats* stats) {
+    if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
+    if (!(tol > 0.0) || !(tol < 1.0))
+        return fail(ctx, BKS_ERR_INVALID_ARG, "tol must be in (0, 1)");
+    return solve_entry(ctx, A, k, q_max, seed, pi, Z, sigma, V, opts, stats, true, false, false, tol);
 }
 
 bks_status bks_simul_iter(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,

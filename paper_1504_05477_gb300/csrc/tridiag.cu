@@ -88,8 +88,9 @@ TdShape td_pick(int w) {
 // j+1 publishes it.  After the cluster barrier each CTA gathers p, K = (tau / 2) p . v,
 // w = p - K v, updates its columns, A -= v w^T + w v^T, and the published column, which
 // becomes the next step's xa (double-buffered).  Per step: one cluster barrier and two
-// CTA barriers.  Outputs: dT (w), eT (w - 1), tau (w - 1) and the reflectors: row j of V
-// holds v_j in columns j+1..w-1.
+// CTA barriers.  Outputs: dT (w), eT (w - 1), tau (w - 1), max_i M_ii in tau[w - 1] (the
+// eigenvalues of M are those of T times it) and the reflectors: row j of V holds v_j in
+// columns j+1..w-1.
 template <typename T>
 __global__ void __launch_bounds__(TD_NT) tridiag_kernel(const T* __restrict__ M, int w, int tpc, int64_t wp,
                                                         T* __restrict__ dT, T* __restrict__ eT,
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(TD_NT) tridiag_kernel(const T* __restrict__ M,
     mx = T(0);
     for (int q = 0; q < TD_NW; ++q) mx = fmax(mx, red[q]);
     const T sc = (mx > T(0) && isfinite(mx)) ? T(1) / mx : T(1);
+    if (r == 0 && tid == 0) tau_out[w - 1] = T(1) / sc;   // eigenvalues of M = those of T times this
     for (int l0 = 0; l0 < nl; l0 += 8)
         for (int i = tid; i < w; i += TD_NT) {
             T rv[8];
@@ -586,21 +588,13 @@ struct TdScratch {
 
 size_t tridiag_scratch_elems(int w, int m) { return TdScratch(w, m).total; }
 
+namespace {
+
+// Tridiagonal reduction and multisection of the m largest eigenvalues (scaled by
+// 1 / max_i M_ii, the inverse of the scale in tau[w - 1]).
 template <typename T>
-bool topk_tridiag(Exec& ex, int w, const T* M, int m, T* Vt, int64_t ldv, T* scratch, const OrthWs& ows) {
-    if (!tridiag_fits<T>(w, m)) return false;
+bool reduce_and_bisect(Exec& ex, int w, const T* M, int m, T* scratch, const TdScratch& L) {
     const TdShape sh = td_pick<T>(w);
-    const int64_t ldx = round_up(w, 32);
-    const TdScratch L(w, m);
-    T* dT = scratch + L.dT;
-    T* eT = scratch + L.eT;
-    T* tau = scratch + L.tau;
-    T* tn = scratch + L.tn;
-    T* lam = scratch + L.lam;
-    T* V = scratch + L.V;
-    T* X = scratch + L.X;
-    T* Xtmp = scratch + L.Xtmp;
-    T* Tw = scratch + L.Tw;
     auto kern = tridiag_kernel<T>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sh.smem)) != cudaSuccess ||
         (sh.C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
@@ -619,18 +613,51 @@ bool topk_tridiag(Exec& ex, int w, const T* M, int m, T* Vt, int64_t ldv, T* scr
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, kern, M, w, sh.tpc, sh.wp, dT, eT, tau, V) != cudaSuccess) {
+    if (cudaLaunchKernelEx(&cfg, kern, M, w, sh.tpc, sh.wp, scratch + L.dT, scratch + L.eT, scratch + L.tau,
+                           scratch + L.V) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     const int wpb = 8;   // eigenvalues (warps) per CTA of the multisection
-    bisect_kernel<T><<<(m + wpb - 1) / wpb, wpb * 32, size_t(2) * w * sizeof(T), ex.stream>>>(dT, eT, w, m, lam, tn);
+    bisect_kernel<T><<<(m + wpb - 1) / wpb, wpb * 32, size_t(2) * w * sizeof(T), ex.stream>>>(
+        scratch + L.dT, scratch + L.eT, w, m, scratch + L.lam, scratch + L.tn);
+    ex.launches += 2;
+    return true;
+}
+
+}  // namespace
+
+template <typename T>
+bool topk_values(Exec& ex, int w, const T* M, int m, T* scratch, const T** lam, const T** inv_scale) {
+    if (!tridiag_fits<T>(w, m)) return false;
+    const TdScratch L(w, m);
+    if (!reduce_and_bisect(ex, w, M, m, scratch, L)) return false;
+    *lam = scratch + L.lam;
+    *inv_scale = scratch + L.tau + (w - 1);
+    return true;
+}
+
+template <typename T>
+bool topk_tridiag(Exec& ex, int w, const T* M, int m, T* Vt, int64_t ldv, T* scratch, const OrthWs& ows) {
+    if (!tridiag_fits<T>(w, m)) return false;
+    const int64_t ldx = round_up(w, 32);
+    const TdScratch L(w, m);
+    T* dT = scratch + L.dT;
+    T* eT = scratch + L.eT;
+    T* tau = scratch + L.tau;
+    T* tn = scratch + L.tn;
+    T* lam = scratch + L.lam;
+    T* V = scratch + L.V;
+    T* X = scratch + L.X;
+    T* Xtmp = scratch + L.Xtmp;
+    T* Tw = scratch + L.Tw;
+    if (!reduce_and_bisect(ex, w, M, m, scratch, L)) return false;
     const int vpc = invit_vpc<T>(w);
     const size_t ismem = invit_smem<T>(w, vpc);
     if (ismem > 48 * 1024)
         cudaFuncSetAttribute(invit_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ismem));
     invit_kernel<T><<<(m + vpc - 1) / vpc, vpc, ismem, ex.stream>>>(dT, eT, lam, tn, w, m, X, ldx, ex.status);
-    ex.launches += 3;
+    ex.launches += 1;
     // orthonormal eigenvector basis (CholeskyQR2 of the m x w block; thin blocks keep
     // their pad rows at zero, so the scratch block starts zeroed)
     cudaMemsetAsync(Xtmp, 0, size_t(m) * ldx * sizeof(T), ex.stream);
@@ -654,5 +681,7 @@ template bool tridiag_fits<float>(int, int);
 template bool tridiag_fits<double>(int, int);
 template bool topk_tridiag<float>(Exec&, int, const float*, int, float*, int64_t, float*, const OrthWs&);
 template bool topk_tridiag<double>(Exec&, int, const double*, int, double*, int64_t, double*, const OrthWs&);
+template bool topk_values<float>(Exec&, int, const float*, int, float*, const float**, const float**);
+template bool topk_values<double>(Exec&, int, const double*, int, double*, const double**, const double**);
 
 }  // namespace bks

@@ -371,3 +371,41 @@ def test_gradient_terms_are_all_needed():
     gg = 2 * (ak - t)
     comp = (gg @ v[:, :k] - u @ (u.T @ (gg @ v[:, :k]))) @ v[:, :k].T
     assert np.linalg.norm(comp) / np.linalg.norm(g_fd) > 1e-3
+
+
+# ------------------------------------------------------------- adaptive iteration count
+def test_adaptive_stops_once_the_space_covers_the_rank():
+    # rank 20, k = 10: two blocks span range(A), so the third adds nothing and the
+    # iteration stops there with q = 2; the result is block_krylov's at q = 2
+    sig = np.concatenate([1.0 / np.arange(1, 21), np.zeros(20)])
+    a, u, v = _planted(60, 40, sig, 13)
+    pi = synth.gaussian_pi(4, 40, 10, np.float64)
+    res, deltas = krylov.block_krylov_adaptive(a, 10, 8, 1e-10, pi)
+    assert res.q_eff == 2 and deltas[-1] < 1e-12 and deltas[0] > 1e-6
+    ref = krylov.block_krylov(a, 10, 2, pi)
+    assert np.array_equal(res.sigma, ref.sigma)
+    assert np.max(np.abs(res.sigma - sig[:10]) / sig[:10]) < 1e-12
+
+
+def test_adaptive_runs_q_max_when_tol_is_never_met():
+    a, _, _, _ = synth.dense_planted_small()
+    pi = synth.gaussian_pi(1, 300, 10, np.float64)
+    res, deltas = krylov.block_krylov_adaptive(a, 10, 3, 1e-15, pi)
+    assert res.q_eff == 3 and len(deltas) == 2 and min(deltas) > 1e-15   # tested after blocks 2 and 3
+    ref = krylov.block_krylov(a, 10, 3, pi)
+    assert np.array_equal(res.sigma, ref.sigma)
+
+
+def test_adaptive_changes_are_nonnegative_and_ritz_values_monotone():
+    # nested spaces: Ritz values only grow (Courant-Fischer), so every change is an increase
+    a, _ = synth.dense_planted_noisy(n=800, d=500, rank=100, seed=6)
+    pi = synth.gaussian_pi(2, 500, 8, np.float64)
+    op = krylov.dense_op(a)
+    prev = None
+    for q in range(0, 5):
+        s = krylov.block_krylov(a, 8, q, pi).sigma
+        if prev is not None:
+            assert np.all(s >= prev - 1e-12 * s[0])
+        prev = s
+    res, deltas = krylov.block_krylov_adaptive(a, 8, 6, 1e-6, pi)
+    assert all(d >= 0 for d in deltas) and res.q_eff <= 6
