@@ -26,6 +26,8 @@ struct Params {
     int maxseg;
     int* status;
     int accumulate;    // 1: out += result (out is read first), 0: out = result
+    unsigned* tile_cnt;   // non-null: per-tile arrival counters (zeroed before the launch); the
+                          // last CTA to finish a cut tile sums its partials (no fix-up launch)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {

@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc_product_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmXh,
                       const __grid_constant__ CUtensorMap tmXl, Params p) {
     extern __shared__ unsigned char smem_dyn[];
+    __shared__ int fix_last;   // epilogue: this CTA completes the cut tile it just wrote
     // 1024-byte alignment for the swizzled tiles
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
@@ -399,6 +400,39 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int j = 0; j < CP; ++j)
                     if (j < p.c) dst[int64_t(j) * stride] = run[j];
             }
+            if (!whole && p.tile_cnt != nullptr) {
+                // cut tile: the last of its CTAs to get here adds the partials in CTA order
+                // (for up to 8 CTAs per tile the order of tc_fixup_kernel: the same bits)
+                const int64_t G = gridDim.x, U = p.tiles * p.cpt;
+                const int64_t c_first = ((t * p.cpt + 1) * G - 1) / U;
+                const int64_t c_last = (((t + 1) * p.cpt) * G - 1) / U;
+                int ncontrib = 0;
+                for (int64_t cc = c_first; cc <= c_last; ++cc) ncontrib += ((cc + 1) * U) / G != (cc * U) / G;
+                __threadfence();
+                asm volatile("bar.sync 1, 128;" ::: "memory");   // the four epilogue warps
+                if (m == 0) fix_last = atomicAdd(&p.tile_cnt[t], 1u) == unsigned(ncontrib - 1);
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (fix_last) {
+                    __threadfence();
+                    float v[CP];
+#pragma unroll
+                    for (int j = 0; j < CP; ++j) v[j] = 0.f;
+                    for (int64_t cc = c_first; cc <= c_last; ++cc) {
+                        const int64_t start = (cc * U) / G;
+                        if (((cc + 1) * U) / G == start) continue;
+                        const float* src = p.part + ((cc * p.maxseg + (t - start / p.cpt)) * CP) * BM + m;
+#pragma unroll
+                        for (int j = 0; j < CP; ++j)
+                            if (j < p.c) v[j] += __ldcg(src + int64_t(j) * BM);
+                    }
+                    if (row < p.rows_out) {
+                        float* o = p.out + row;
+#pragma unroll
+                        for (int j = 0; j < CP; ++j)
+                            if (j < p.c) o[int64_t(j) * p.ldo] = p.accumulate ? o[int64_t(j) * p.ldo] + v[j] : v[j];
+                    }
+                }
+            }
         }
     }
 
@@ -507,7 +541,7 @@ void fixup(Exec& ex, const Params& p, int G) {
 int64_t partial_floats(int64_t rows_out, int64_t len, int kc, int cp, int num_sms) {
     const int64_t tiles = (rows_out + BM - 1) / BM, cpt = (len + kc - 1) / kc;
     const int64_t U = tiles * cpt, G = grid_for_units(U, num_sms), per = (U + G - 1) / G;
-    return G * (per / cpt + 2) * cp * BM;
+    return G * (per / cpt + 2) * cp * BM + tiles + 32;   // partial tiles, then the tile counters
 }
 
 size_t smem_bytes(int cp) {
@@ -574,10 +608,18 @@ bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda,
         const int Gc = grid_for_units(U, G);
         const int64_t per = (U + Gc - 1) / Gc;
         p.maxseg = int(per / p.cpt + 2);
-        if (int64_t(Gc) * p.maxseg * cp * BM > part_cap) return false;
+        const int64_t slots = int64_t(Gc) * p.maxseg * cp * BM;
+        if (slots > part_cap) return false;
         p.part = part;
         p.status = ex.status;
         p.accumulate = subtract ? 1 : 0;
+        // cut tiles are completed inside the kernel when at most three CTAs share a tile (the
+        // completing CTA then adds one or two partials) and the counters fit after the slots;
+        // finer splits (short products such as M = B^T B) keep the parallel fix-up kernel
+        const int64_t max_share = (p.cpt + per - 1) / per + 1;
+        p.tile_cnt = max_share <= 3 && slots + p.tiles <= part_cap ? reinterpret_cast<unsigned*>(part + slots)
+                                                                   : nullptr;
+        if (p.tile_cnt) cudaMemsetAsync(p.tile_cnt, 0, size_t(p.tiles) * sizeof(unsigned), ex.stream);
         const size_t smem = smem_bytes(cp);
         cudaError_t err;
         switch (cp) {
@@ -599,7 +641,7 @@ bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda,
             cudaGetLastError();
             return false;
         }
-        fixup(ex, p, Gc);
+        if (!p.tile_cnt) fixup(ex, p, Gc);
         ex.launches++;
     }
     return true;
