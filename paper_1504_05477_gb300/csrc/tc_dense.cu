@@ -613,11 +613,11 @@ bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda,
         p.part = part;
         p.status = ex.status;
         p.accumulate = subtract ? 1 : 0;
-        // cut tiles are completed inside the kernel when at most three CTAs share a tile (the
-        // completing CTA then adds one or two partials) and the counters fit after the slots;
+        // cut tiles are completed inside the kernel when at most four CTAs share a tile (the
+        // completing CTA then adds up to four partials) and the counters fit after the slots;
         // finer splits (short products such as M = B^T B) keep the parallel fix-up kernel
         const int64_t max_share = (p.cpt + per - 1) / per + 1;
-        p.tile_cnt = max_share <= 3 && slots + p.tiles <= part_cap ? reinterpret_cast<unsigned*>(part + slots)
+        p.tile_cnt = max_share <= 4 && slots + p.tiles <= part_cap ? reinterpret_cast<unsigned*>(part + slots)
                                                                    : nullptr;
         if (p.tile_cnt) cudaMemsetAsync(p.tile_cnt, 0, size_t(p.tiles) * sizeof(unsigned), ex.stream);
         const size_t smem = smem_bytes(cp);
