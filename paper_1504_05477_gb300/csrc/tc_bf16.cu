@@ -108,23 +108,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (lane == 0) {
             int last[8];
             for (int s = 0; s < 8; ++s) last[s] = -1;
-            int64_t i = 0;
-            for (int64_t u = ustart; u < uend; ++u, ++i) {
-                const int s = int(i % C::STAGES);
-                if (!wait_bar(&sm->empty[s], uint32_t(((i / C::STAGES) & 1) ^ 1), abort_flag, p.status)) break;
-                const int64_t t = u / p.cpt, kc = u % p.cpt;
+            UnitWalk w(ustart, p.cpt);
+            int s = 0, ph = 0;
+            for (int64_t u = ustart; u < uend; ++u, w.next()) {
+                if (!wait_bar(&sm->empty[s], uint32_t(ph ^ 1), abort_flag, p.status)) break;
+                const int t = int(w.t), kc = w.kc;
                 unsigned char* st = ring + s * C::STAGE;
                 mbar_expect_tx(&sm->full[s], C::STAGE);
                 if (p.mode == 0) {   // A X: box {64 (d), 128 (n)}, K-major
-                    tma_load_2d(st, &tmA, int(kc * KC), int(t * BM), &sm->full[s]);
+                    tma_load_2d(st, &tmA, kc * KC, t * BM, &sm->full[s]);
                 } else {             // A^T X: two boxes {64 (d), 64 (n)}, MN-major halves
-                    tma_load_2d(st, &tmA, int(t * BM), int(kc * KC), &sm->full[s]);
-                    tma_load_2d(st + A_BYTES / 2, &tmA, int(t * BM + 64), int(kc * KC), &sm->full[s]);
+                    tma_load_2d(st, &tmA, t * BM, kc * KC, &sm->full[s]);
+                    tma_load_2d(st + A_BYTES / 2, &tmA, t * BM + 64, kc * KC, &sm->full[s]);
                 }
 #pragma unroll
                 for (int pc = 0; pc < NP; ++pc)
-                    tma_load_2d(st + A_BYTES + pc * CP * 128, &tmX, int(kc * KC), pc * p.c, &sm->full[s]);
-                last[s] = int((i / C::STAGES) & 1);
+                    tma_load_2d(st + A_BYTES + pc * CP * 128, &tmX, kc * KC, pc * p.c, &sm->full[s]);
+                last[s] = ph;
+                if (++s == C::STAGES) { s = 0; ph ^= 1; }
             }
             for (int s = 0; s < C::STAGES; ++s) drain_bar(&sm->full[s], last[s]);
         }
@@ -132,17 +133,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16(CP, p.mode);
-            int64_t i = 0;
+            int i = 0;
             int sub = -1;
             bool first = true;
+            UnitWalk w(ustart, p.cpt);
             for (int64_t u = ustart; u < uend; ++u, ++i) {
-                if (window_start(u, ustart, p.cpt, C::FL)) {
+                if (u == ustart || w.kc % C::FL == 0) {   // a new accumulation window
                     ++sub;
                     if (!wait_bar(&sm->acc_empty[sub & 1], uint32_t(((sub >> 1) & 1) ^ 1), abort_flag, p.status)) break;
                     tc_fence_after();
                     first = true;
                 }
-                const int s = int(i % C::STAGES);
+                const int s = i % C::STAGES;
                 if (!wait_bar(&sm->full[s], uint32_t((i / C::STAGES) & 1), abort_flag, p.status)) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + uint32_t(sub & 1) * C::ACC_STRIDE;
@@ -159,7 +161,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 first = false;
                 umma_commit(&sm->empty[s]);
-                if (u + 1 == uend || window_start(u + 1, ustart, p.cpt, C::FL))
+                w.next();
+                if (u + 1 == uend || w.kc % C::FL == 0)   // the next unit opens a window
                     umma_commit(&sm->acc_full[sub & 1]);
             }
             umma_commit(&sm->drain);
@@ -181,8 +184,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
             for (int j = 0; j < CP; ++j) run[j] = 0.f;
             while (u < seg_end) {
-                int64_t w_end = u + 1;
-                while (w_end < seg_end && !window_start(w_end, ustart, p.cpt, C::FL)) ++w_end;
+                // the window ends at the next chunk that is a multiple of FL, or at seg_end
+                const int kc = int(u - t * p.cpt);
+                int64_t w_end = u + (C::FL - kc % C::FL);
+                if (w_end > seg_end) w_end = seg_end;
                 ++sub;
                 if (!wait_bar(&sm->acc_full[sub & 1], uint32_t((sub >> 1) & 1), abort_flag, p.status)) {
                     ok = false;
@@ -231,12 +236,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // x (rows x len thin, pitch ld) -> np BF16 pieces, piece p at rows [p*rows, (p+1)*rows).
+// Row r = blockIdx.y; the x blocks stride along it.
 __global__ void bf16_split_kernel(const float* __restrict__ x, int rows, int64_t len, int64_t ld, int np,
                                   __nv_bfloat16* __restrict__ xb) {
-    const int64_t total = int64_t(rows) * len;
-    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
-         e += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t r = e / len, l = e % len;
+    const int64_t r = blockIdx.y;
+    for (int64_t l = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; l < len;
+         l += int64_t(gridDim.x) * blockDim.x) {
         float v = x[r * ld + l];
         for (int pc = 0; pc < np; ++pc) {
             const __nv_bfloat16 b = __float2bfloat16_rn(v);
@@ -290,10 +295,12 @@ bool tc_product_bf16(Exec& ex, const __nv_bfloat16* A, int64_t n, int64_t d, int
         const int cp = (cg + 31) / 32 * 32;
         if (int64_t(np) * cg * ldx > xb_cap) return false;
         {
-            const int64_t total = int64_t(cg) * len;
-            int blocks = int((total + 255) / 256);
-            if (blocks > 4 * G) blocks = 4 * G;
-            bf16_split_kernel<<<blocks, 256, 0, ex.stream>>>(X + int64_t(c0) * ldx, cg, len, ldx, np, xb);
+            int64_t bx = (len + 255) / 256;
+            const int64_t cap = (4 * int64_t(G) + cg - 1) / cg;
+            if (bx > cap) bx = cap;
+            if (bx < 1) bx = 1;
+            bf16_split_kernel<<<dim3(unsigned(bx), unsigned(cg)), 256, 0, ex.stream>>>(X + int64_t(c0) * ldx, cg, len,
+                                                                                      ldx, np, xb);
             ex.launches++;
         }
         CUtensorMap tmX;

@@ -175,11 +175,20 @@ __device__ __forceinline__ void unit_range(int64_t U, int G, int cta, int64_t& s
     e = (int64_t(cta + 1) * U) / G;
 }
 
-// A new accumulation window starts at the CTA's first unit, at every tile boundary and
-// every `flush` chunks within a tile.
-__device__ __forceinline__ bool window_start(int64_t u, int64_t ustart, int64_t cpt, int flush) {
-    return u == ustart || (u % cpt) % flush == 0;
-}
+// Position (tile t, chunk kc) of a CTA's current unit, advanced by one increment per unit:
+// one 64-bit division at the start of the range instead of one per unit (a 64-bit
+// division is a long software sequence, and one per unit capped a role's unit rate).
+struct UnitWalk {
+    int64_t t;
+    int kc, cpt;
+    __device__ UnitWalk(int64_t u, int64_t cpt_) : t(u / cpt_), kc(int(u % cpt_)), cpt(int(cpt_)) {}
+    __device__ __forceinline__ void next() {
+        if (++kc == cpt) {
+            kc = 0;
+            ++t;
+        }
+    }
+};
 
 // Driver-API tensor-map encoder, looked up once.
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn();

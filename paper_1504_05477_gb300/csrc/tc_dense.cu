@@ -141,17 +141,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (lane == 0) {
             int last[RA_MAX];   // phase of the last load issued into each stage (-1: none)
             for (int s = 0; s < RA_MAX; ++s) last[s] = -1;
-            int64_t i = 0;
-            for (int64_t u = ustart; u < uend; ++u, ++i) {
-                const int s = int(i % NRA);
-                if (!wait_bar(&sm->raw_empty[s], uint32_t(((i / NRA) & 1) ^ 1), abort_flag, p.status)) break;
-                const int64_t t = u / p.cpt, kc = u % p.cpt;
+            UnitWalk w(ustart, p.cpt);
+            int s = 0, ph = 0;
+            for (int64_t u = ustart; u < uend; ++u, w.next()) {
+                if (!wait_bar(&sm->raw_empty[s], uint32_t(ph ^ 1), abort_flag, p.status)) break;
                 mbar_expect_tx(&sm->raw_full[s], TILE_BYTES);
                 if (p.mode == 0)   // AX: box {32 (d), 128 (n)}
-                    tma_load_2d(raw + s * TILE_BYTES, &tmA, int(kc * KC), int(t * BM), &sm->raw_full[s]);
+                    tma_load_2d(raw + s * TILE_BYTES, &tmA, w.kc * KC, int(w.t * BM), &sm->raw_full[s]);
                 else               // ATX: box {128 (d), 32 (n)}
-                    tma_load_2d(raw + s * TILE_BYTES, &tmA, int(t * BM), int(kc * KC), &sm->raw_full[s]);
-                last[s] = int((i / NRA) & 1);
+                    tma_load_2d(raw + s * TILE_BYTES, &tmA, int(w.t * BM), w.kc * KC, &sm->raw_full[s]);
+                last[s] = ph;
+                if (++s == NRA) { s = 0; ph ^= 1; }
             }
             // every load issued has landed before shared memory is released (bounded)
             for (int s = 0; s < NRA; ++s) drain_bar(&sm->raw_full[s], last[s]);
@@ -161,16 +161,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (lane == 0) {
             int last[XR_MAX];
             for (int o = 0; o < XR_MAX; ++o) last[o] = -1;
-            int64_t i = 0;
-            for (int64_t u = ustart; u < uend; ++u, ++i) {
-                const int o = int(i % XR);
-                if (!wait_bar(&sm->x_empty[o], uint32_t(((i / XR) & 1) ^ 1), abort_flag, p.status)) break;
-                const int64_t kc = u % p.cpt;
+            UnitWalk w(ustart, p.cpt);
+            int o = 0, ph = 0;
+            for (int64_t u = ustart; u < uend; ++u, w.next()) {
+                if (!wait_bar(&sm->x_empty[o], uint32_t(ph ^ 1), abort_flag, p.status)) break;
                 mbar_expect_tx(&sm->x_full[o], b_bytes);
                 unsigned char* dst = bop + o * b_bytes;
-                tma_load_2d(dst, &tmXh, int(kc * KC), 0, &sm->x_full[o]);
-                tma_load_2d(dst + CP * 128, &tmXl, int(kc * KC), 0, &sm->x_full[o]);
-                last[o] = int((i / XR) & 1);
+                tma_load_2d(dst, &tmXh, w.kc * KC, 0, &sm->x_full[o]);
+                tma_load_2d(dst + CP * 128, &tmXl, w.kc * KC, 0, &sm->x_full[o]);
+                last[o] = ph;
+                if (++o == XR) { o = 0; ph ^= 1; }
             }
             for (int o = 0; o < XR; ++o) drain_bar(&sm->x_full[o], last[o]);
         }
@@ -178,19 +178,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ---------------------------------------------------------------- MMA issuer
         if (lane == 0) {
             const uint32_t id_full = idesc_tf32(2 * CP), id_half = idesc_tf32(CP);
-            int64_t i = 0;
+            int i = 0;
             int sub = -1;   // accumulation window: at most FLUSH chunks per TMEM accumulator
             bool first = true;
+            UnitWalk w(ustart, p.cpt);
             for (int64_t u = ustart; u < uend; ++u, ++i) {
-                const int64_t t = u / p.cpt;
-                if (window_start(u, ustart, p.cpt, FLUSH)) {
+                if (u == ustart || w.kc % FLUSH == 0) {   // a new accumulation window
                     ++sub;
                     if (!wait_bar(&sm->acc_empty[sub & 1], uint32_t(((sub >> 1) & 1) ^ 1), abort_flag, p.status)) break;
                     tc_fence_after();
                     first = true;
                 }
-                (void)t;
-                const int o = int(i % NOP), xs = int(i % XR);
+                const int o = i % NOP, xs = i % XR;
                 const uint32_t par = uint32_t((i / NOP) & 1);
                 if (!wait_bar(&sm->conv_full[o], par, abort_flag, p.status)) break;
                 if (!wait_bar(&sm->x_full[xs], uint32_t((i / XR) & 1), abort_flag, p.status)) break;
@@ -219,7 +218,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 first = false;
                 umma_commit(&sm->op_empty[o]);
                 umma_commit(&sm->x_empty[xs]);
-                if (u + 1 == uend || window_start(u + 1, ustart, p.cpt, FLUSH))
+                w.next();
+                if (u + 1 == uend || w.kc % FLUSH == 0)   // the next unit opens a window
                     umma_commit(&sm->acc_full[sub & 1]);
             }
             // drain: every MMA issued so far has completed before TMEM is released
@@ -229,13 +229,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     } else if (warp <= 6) {
         // ---------------------------------------------------------------- converters
         const int ct = tid - 96;   // 0..127
-        int64_t i = 0;
+        int i = 0;
         if constexpr (TS) {
             // thread = TMEM lane = row m of the A tile (a warp reaches lanes 32 (warp % 4) ..)
             const int m = (warp & 3) * 32 + lane;
             const uint32_t lane_addr = uint32_t((warp & 3) * 32) << 16;
             for (int64_t u = ustart; u < uend; ++u, ++i) {
-                const int s = int(i % NRA), o = int(i % NOP);
+                const int s = i % NRA, o = i % NOP;
                 if (!wait_bar(&sm->raw_full[s], uint32_t((i / NRA) & 1), abort_flag, p.status)) break;
                 const unsigned char* rs = raw + s * TILE_BYTES;
                 uint32_t h[32], l[32];
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
         } else
         for (int64_t u = ustart; u < uend; ++u, ++i) {
-            const int s = int(i % RA), o = int(i % OP);
+            const int s = i % RA, o = i % OP;
             if (!wait_bar(&sm->raw_full[s], uint32_t((i / RA) & 1), abort_flag, p.status)) break;
             if (!wait_bar(&sm->op_empty[o], uint32_t(((i / OP) & 1) ^ 1), abort_flag, p.status)) break;
             const unsigned char* rs = raw + s * TILE_BYTES;
@@ -340,8 +340,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
             for (int j = 0; j < CP; ++j) run[j] = 0.f;
             while (u < seg_end) {
-                int64_t w_end = u + 1;
-                while (w_end < seg_end && !window_start(w_end, ustart, p.cpt, FLUSH)) ++w_end;
+                // the window ends at the next chunk that is a multiple of FLUSH, or at seg_end
+                const int kc = int(u - t * p.cpt);
+                int64_t w_end = u + (FLUSH - kc % FLUSH);
+                if (w_end > seg_end) w_end = seg_end;
                 ++sub;
                 if (!wait_bar(&sm->acc_full[sub & 1], uint32_t((sub >> 1) & 1), abort_flag, p.status)) {
                     ok = false;
@@ -483,12 +485,12 @@ __global__ void __launch_bounds__(FIX_SLOTS * BM) tc_fixup_kernel(Params p, int 
 }
 
 // hi/lo split of sign * x for a thin block (rows x len, row pitch ld; sign = +-1).
+// Row r = blockIdx.y; the x blocks stride along it.
 __global__ void tf32_split_kernel(const float* __restrict__ x, int rows, int64_t len, int64_t ld,
                                   float sign, float* __restrict__ xh, float* __restrict__ xl) {
-    const int64_t total = int64_t(rows) * len;
-    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
-         e += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t r = e / len, l = e % len;
+    const int64_t r = blockIdx.y;
+    for (int64_t l = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; l < len;
+         l += int64_t(gridDim.x) * blockDim.x) {
         const float v = sign * x[r * ld + l];
         const float h = tf32_hi(v);
         xh[r * ld + l] = h;
@@ -582,11 +584,12 @@ bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda,
         float* xhg = xh + int64_t(c0) * ldx;
         float* xlg = xl + int64_t(c0) * ldx;
         {
-            const int64_t total = int64_t(cg) * len;
-            int blocks = int((total + 255) / 256);
-            if (blocks > 4 * G) blocks = 4 * G;
-            tf32_split_kernel<<<blocks, 256, 0, ex.stream>>>(Xg, cg, len, ldx, subtract ? -1.f : 1.f,
-                                                             xhg, xlg);
+            int64_t bx = (len + 255) / 256;
+            const int64_t cap = (4 * int64_t(G) + cg - 1) / cg;
+            if (bx > cap) bx = cap;
+            if (bx < 1) bx = 1;
+            tf32_split_kernel<<<dim3(unsigned(bx), unsigned(cg)), 256, 0, ex.stream>>>(
+                Xg, cg, len, ldx, subtract ? -1.f : 1.f, xhg, xlg);
             ex.launches++;
         }
         CUtensorMap tmXh, tmXl;
