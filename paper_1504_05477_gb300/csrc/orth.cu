@@ -366,7 +366,7 @@ __host__ __device__ inline int pad_rows(int c) {
     return p > 4 ? p : 4;
 }
 struct Layout {
-    int coef, ach, wout, hbuf, pbuf, c2t, p1t, red, total, stage, pad;
+    int coef, ach, wout, hbuf, pbuf, red, total, stage, pad;
     __host__ __device__ Layout(int m, int c) {
         const int R = m + c;
         pad = pad_rows(c);
@@ -376,10 +376,8 @@ struct Layout {
         // scratch used outside the chunk loops, aliasing the stages
         hbuf = ach;
         pbuf = hbuf + r4(c * c);
-        c2t = pbuf + r4(c * c);
-        p1t = c2t + r4(m * c);
         red = ach;                 // SLOTS x 32 x 4 doubles = 2048 floats
-        int scratch_end = p1t + r4(c * r4(c));
+        int scratch_end = pbuf + r4(c * c);
         if (red + 2 * SLOTS * 32 * 4 > scratch_end) scratch_end = red + 2 * SLOTS * 32 * 4;
         wout = ach + NB * stage;
         if (scratch_end > wout) wout = scratch_end;
@@ -479,6 +477,8 @@ __device__ __forceinline__ void store_rows(float* dst, const float* src, int nro
 // rg, rg + RS, rg + 2 RS, rg + 3 RS; columns j0 .. j0 + TJ - 1), chunk rows l = lsub,
 // lsub + LS, ...; the LS partial tiles are combined by shuffles at the end.  Rows past
 // Ra and columns past c read zero padding or rows whose results are discarded.
+// Consecutive tiles take consecutive rg with the same j0, so a warp's loads of B are one
+// broadcast address and its loads of A hit distinct banks.
 template <int TJ>
 struct GramMap {
     int RS, LS, rg, j0, lsub;
@@ -492,8 +492,8 @@ struct GramMap {
         const int t = threadIdx.x / LS;
         lsub = threadIdx.x % LS;
         on = t < tiles;
-        rg = t / nj;
-        j0 = (t % nj) * TJ;
+        rg = t % RS;
+        j0 = (t / RS) * TJ;
     }
 };
 
@@ -620,8 +620,6 @@ __global__ void __launch_bounds__(NT, 1) orth_fused_kernel(Args a) {
     float* hbuf = sm + L.hbuf;
     float* pbuf = sm + L.pbuf;
     double* red = reinterpret_cast<double*>(sm + L.red);
-    float* c2t = sm + L.c2t;
-    float* p1t = sm + L.p1t;
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
     const int64_t l0 = int64_t(cta) * a.len / G, l1 = int64_t(cta + 1) * a.len / G;
     unsigned phase = 0;
@@ -672,19 +670,30 @@ __global__ void __launch_bounds__(NT, 1) orth_fused_kernel(Args a) {
         });
         if (!reduce(gm, R)) return;
     }
-    // ---- P3: R1 from H - C2^T C2; coefficients [-C2 P1^T; P1^T] with P1 = R1^{-T}
+    // ---- P3: R1 from H - C2^T C2, P1 = R1^{-T}; W1 = (W' - Q C2) P1^T with its Gram
     for (int e = tid; e < R * c; e += NT) coef[(e / c) * cs + e % c] = __ldcg(a.gram + e);
     __syncthreads();
-    {   // H - C2^T C2 by 4 x 4 register tiles
-        const int nt4 = (c + 3) / 4;
-        for (int t = tid; t < nt4 * nt4; t += NT) {
-            const int i0 = (t / nt4) * 4, j0 = (t % nt4) * 4;
-            float h[4][4];
+    {   // H - C2^T C2: 4 x 4 register tiles of the upper triangle (mirrored), each tile's
+        // rows r of C2 split between S adjacent lanes and combined by shuffles
+        const int nt4 = (c + 3) / 4, ntri = nt4 * (nt4 + 1) / 2;
+        int S = 1;
+        while (S < 8 && ntri * S * 2 <= NT) S *= 2;
+        const int t = tid / S, sr = tid % S;
+        int ti = 0, rem = t;
+        while (ti < nt4 && rem >= nt4 - ti) {
+            rem -= nt4 - ti;
+            ++ti;
+        }
+        const bool on = t < ntri;
+        const int i0 = ti * 4, j0 = (ti + rem) * 4;
+        float h[4][4];
 #pragma unroll
-            for (int x = 0; x < 4; ++x)
+        for (int x = 0; x < 4; ++x)
 #pragma unroll
-                for (int y = 0; y < 4; ++y) h[x][y] = 0.f;
-            for (int r = 0; r < m; ++r) {
+            for (int y = 0; y < 4; ++y) h[x][y] = 0.f;
+        if (on) {
+#pragma unroll 4
+            for (int r = sr; r < m; r += S) {
                 const float4 u = *reinterpret_cast<const float4*>(coef + r * cs + i0);
                 const float4 v = *reinterpret_cast<const float4*>(coef + r * cs + j0);
                 const float uu[4] = {u.x, u.y, u.z, u.w}, vv[4] = {v.x, v.y, v.z, v.w};
@@ -693,70 +702,48 @@ __global__ void __launch_bounds__(NT, 1) orth_fused_kernel(Args a) {
 #pragma unroll
                     for (int y = 0; y < 4; ++y) h[x][y] = fmaf(uu[x], vv[y], h[x][y]);
             }
+        }
+        for (int off = 1; off < S; off <<= 1)   // the S lanes of a tile are adjacent
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) h[x][y] += __shfl_xor_sync(0xffffffffu, h[x][y], off);
+        if (on && sr == 0) {
 #pragma unroll
             for (int x = 0; x < 4; ++x)
 #pragma unroll
                 for (int y = 0; y < 4; ++y) {
                     const int i = i0 + x, j = j0 + y;
-                    if (i < c && j < c) hbuf[i * c + j] = coef[(m + i) * cs + j] - h[x][y];
+                    if (i < c && j < c && i <= j) {
+                        const float v = coef[(m + i) * cs + j] - h[x][y];
+                        hbuf[i * c + j] = v;
+                        hbuf[j * c + i] = v;
+                    }
                 }
         }
     }
     __syncthreads();
     chol_inv_block(hbuf, c, c, pbuf, c, a.status, a.shifted_flag);
     __syncthreads();
-    // E = -C2 P1^T (m x c) as an apply over the transposed C2: lanes run over rows r
-    for (int e = tid; e < m * c; e += NT) {
-        const int r = e / c, b = e % c;
-        c2t[b * m + r] = coef[r * cs + b];
-    }
-    for (int e = tid; e < c * cs; e += NT) {
-        const int b = e / cs, j = e % cs;
-        p1t[e] = j < c ? pbuf[j * c + b] : 0.f;
-    }
-    __syncthreads();
-    {
-        const int lane = tid & 31, w = tid >> 5;
-        const int JW = r4((c + 7) / 8), j0 = w * JW;
-        if (j0 < c)
-            for (int r0 = 0; r0 < m; r0 += 32) {
-                const int r = r0 + lane;
-                float e8[8];
-#pragma unroll
-                for (int t = 0; t < 8; ++t) e8[t] = 0.f;
-                if (r < m) {
-#pragma unroll 4
-                    for (int b = 0; b < c; ++b) {
-                        const float x = c2t[b * m + r];
-                        const float4 p0 = *reinterpret_cast<const float4*>(p1t + b * cs + j0);
-                        e8[0] = fmaf(x, p0.x, e8[0]);
-                        e8[1] = fmaf(x, p0.y, e8[1]);
-                        e8[2] = fmaf(x, p0.z, e8[2]);
-                        e8[3] = fmaf(x, p0.w, e8[3]);
-                        if (JW == 8) {
-                            const float4 p1 = *reinterpret_cast<const float4*>(p1t + b * cs + j0 + 4);
-                            e8[4] = fmaf(x, p1.x, e8[4]);
-                            e8[5] = fmaf(x, p1.y, e8[5]);
-                            e8[6] = fmaf(x, p1.z, e8[6]);
-                            e8[7] = fmaf(x, p1.w, e8[7]);
-                        }
-                    }
-#pragma unroll
-                    for (int t = 0; t < 8; ++t)
-                        if (t < JW && j0 + t < c) coef[r * cs + j0 + t] = -e8[t];
-                }
-            }
-    }
+    // rows m .. m + c - 1 of coef (H, no longer needed) take P1^T; rows 0 .. m - 1 keep C2
     for (int e = tid; e < c * c; e += NT) {
         const int b = e / c, j = e % c;
-        coef[(m + b) * cs + j] = p1t[b * cs + j];
+        coef[(m + b) * cs + j] = pbuf[j * c + b];
     }
     __syncthreads();
     {
         const GramMap<TJ> gm(c, c);
         zero();
         stream_chunks(ach, L.stage, a.Q, m, a.W, c, a.ld, l0, l1, [&](float* st, int64_t lb) {
-            apply_chunk(wout, coef, cs, st, R, nullptr, c, false);
+            float* wrows = st + m * LCP;
+            if (m > 0) {   // W' - Q C2, written over the chunk's W' rows
+                apply_chunk(wout, coef, cs, st, m, wrows, c, true);
+                __syncthreads();
+                for (int e = tid; e < c * LC; e += NT)
+                    wrows[(e / LC) * LCP + e % LC] = wout[(e / LC) * LCP + e % LC];
+                __syncthreads();
+            }
+            apply_chunk(wout, coef + m * cs, cs, wrows, c, nullptr, c, false);
             __syncthreads();
             store_rows(a.Wtmp, wout, c, a.ld, lb, l1);
             gram_acc<TJ>(acc, gm, wout, wout);

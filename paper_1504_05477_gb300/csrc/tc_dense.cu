@@ -11,8 +11,9 @@
 //
 // One persistent CTA per SM.  The (tile, 32-deep chunk) units of the whole product are
 // dealt out in equal contiguous ranges (stream-K); a tile cut between CTAs is summed
-// by a fix-up kernel in CTA order, so results are deterministic.
-//   warp 0      TMA: raw A tiles -> 6-deep ring
+// in CTA order (by the last of them to finish, or by a fix-up kernel), so results are
+// deterministic.
+//   warp 0      TMA: raw A tiles -> ring (6 deep; 8-10 when A comes from tensor memory)
 //   warp 1      TMA: [hi(X) | lo(X)] tiles -> their own ring (2 or 4 deep)
 //   warp 2      tcgen05.mma issue (one thread); owns the TMEM allocation
 //   warps 3-6   converters: raw A -> hi(A), lo(A) in the UMMA K-major 128B-swizzled
@@ -28,15 +29,19 @@ namespace tc {
 constexpr int KC = 32;             // contraction depth per chunk (128 bytes of FP32)
 constexpr int RA = 6;              // raw A ring depth
 constexpr int OP = 2;              // converted A (hi / lo) ring depth
-// ring depth of the [hi(X) | lo(X)] tiles, streamed from L2 once per chunk: as deep as
-// shared memory allows, so their L2 round trips overlap
-__host__ __device__ constexpr int x_ring(int cp) { return cp <= 32 ? 4 : 2; }
+// ring depth of the [hi(X) | lo(X)] tiles, streamed from L2 once per chunk.  A stage is
+// refilled only after the MMAs of its chunk complete, so the ring must cover an L2 round
+// trip plus the MMA time: 2 stages held a 64-column product to about one chunk per
+// 0.7 us, 4 do not limit it.
+__host__ __device__ constexpr int x_ring(int cp) { return cp <= 64 ? 4 : 2; }
 constexpr int XR_MAX = 6;
 // Tiles of up to 64 columns take A from tensor memory ("TS" form): the converter writes
 // hi(A) and lo(A) into OPT TMEM stages next to the two accumulators instead of into shared
-// memory, which frees shared memory for a RAT-deep raw A ring.
+// memory, which frees shared memory for a deeper raw A ring.
 __host__ __device__ constexpr bool ts_form(int cp) { return cp <= 64; }
-constexpr int RAT = 10;            // raw A ring depth (TS form)
+// raw A ring depth (TS form): the rest of the shared memory after the X ring
+__host__ __device__ constexpr int raw_ring_ts(int cp) { return cp <= 32 ? 10 : 8; }
+constexpr int RAT = 10;            // deepest raw A ring (TS form)
 constexpr int OPT = 4;             // converted A stages in TMEM (TS form)
 constexpr int ACOL = 256;          // first TMEM column of the A stages (TS form)
 constexpr int RA_MAX = RAT > RA ? RAT : RA;
@@ -91,7 +96,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
     constexpr bool TS = ts_form(CP);
-    constexpr int NRA = TS ? RAT : RA;                           // raw A ring depth
+    constexpr int NRA = TS ? raw_ring_ts(CP) : RA;               // raw A ring depth
     constexpr int NOP = TS ? OPT : OP;                           // converted A stages
     constexpr uint32_t ACC_STRIDE = TS ? 2 * CP : 256;           // TMEM columns per accumulator
     const uint32_t b_bytes = uint32_t(2 * CP) * 128u;
@@ -548,7 +553,7 @@ int64_t partial_floats(int64_t rows_out, int64_t len, int kc, int cp, int num_sm
 
 size_t smem_bytes(int cp) {
     if (ts_form(cp))
-        return size_t(RAT) * TILE_BYTES + size_t(x_ring(cp)) * 2 * cp * 128 + sizeof(Smem) + 1024;
+        return size_t(raw_ring_ts(cp)) * TILE_BYTES + size_t(x_ring(cp)) * 2 * cp * 128 + sizeof(Smem) + 1024;
     return size_t(RA) * TILE_BYTES + size_t(2 * OP) * TILE_BYTES + size_t(x_ring(cp)) * 2 * cp * 128 +
            sizeof(Smem) + 1024;
 }
