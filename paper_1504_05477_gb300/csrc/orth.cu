@@ -133,17 +133,17 @@ __global__ void chol_inv_kernel(const T* __restrict__ G, int64_t ldg, int c, T* 
 }
 
 // P = L^{-1} = R^{-T} for G = L L^T (c <= 128) by symmetric elimination on [G | I]
-// with the elimination rows kept in registers: each thread owns a 4 x 4 tile of the
+// with the elimination rows kept in registers: each thread owns a 4 x TC tile of the
 // trailing matrix S and of the lower-triangular E.  Step j publishes row j of S and E
 // (double-buffered, one barrier per step) and every thread updates its tiles:
 //   S[i][l] -= (S[i][j] / d_j) S[j][l],  E[i][l] -= (S[i][j] / d_j) E[j][l]   (i > j)
 // with the pivot d_j = S[j][j].  At the end E = L_unit^{-1} for G = L_unit D L_unit^T,
 // so L^{-1} = D^{-1/2} E.  Same breakdown handling as chol_inv_kernel.
-constexpr int TR = 4, TC = 8;   // register tile: rows x columns per thread (c <= 128: 512 threads)
-// Block-wide device routine (needs (c/4)(c/8) threads, all threads of the block call it;
-// G and P may live in global or shared memory).
-__device__ void chol_inv_block(const float* G, int64_t ldg, int c, float* P, int64_t ldp, int* status,
-                               int* shifted_flag) {
+constexpr int TR = 4;   // register tile rows per thread; columns TC = 4 when the block has
+                        // (c/4)^2 threads (c <= 64 on 256 threads), else 8 (c <= 128: 512 threads)
+template <int TC>
+__device__ void chol_inv_block_t(const float* G, int64_t ldg, int c, float* P, int64_t ldp, int* status,
+                                 int* shifted_flag) {
     __shared__ __align__(16) float rowS[2][128];
     __shared__ __align__(16) float rowE[2][128];
     __shared__ double trace_s;
@@ -152,16 +152,12 @@ __device__ void chol_inv_block(const float* G, int64_t ldg, int c, float* P, int
     const bool active = tid < ntr * ntc;
     const int ti = active ? tid / ntc : 0, tj = active ? tid % ntc : 0;
     const int r0 = ti * TR, c0 = tj * TC;
-    if (tid == 0) trace_s = 0.0;
-    __syncthreads();
     bool nonfin = false;
     for (int a = 0; a < TR; ++a)
         for (int b = 0; b < TC; ++b) {
             const int i = r0 + a, l = c0 + b;
             if (!active || i >= c || l >= c) continue;
-            const float g = G[int64_t(i) * ldg + l];
-            nonfin |= !isfinite(g);
-            if (i == l) atomicAdd(&trace_s, double(g));
+            nonfin |= !isfinite(G[int64_t(i) * ldg + l]);
         }
     if (__syncthreads_or(nonfin)) {
         if (tid == 0) atomicOr(status, ST_NONFINITE);
@@ -205,16 +201,18 @@ __device__ void chol_inv_block(const float* G, int64_t ldg, int c, float* P, int
                 break;
             }
             if (!active || r0 + TR - 1 < j) continue;   // rows of this tile are all done
-            // branch-free update: row j of S and E read once (c0 is a multiple of 8), rows
+            // branch-free update: row j of S and E read once (c0 is a multiple of 4), rows
             // at or above the pivot get a zero multiplier, columns pick S (l > j) or E
-            const float inv = 1.f / d;
-            const float4 sa = *reinterpret_cast<const float4*>(&rowS[par][c0]);
-            const float4 sb = *reinterpret_cast<const float4*>(&rowS[par][c0 + 4]);
-            const float4 ea = *reinterpret_cast<const float4*>(&rowE[par][c0]);
-            const float4 eb = *reinterpret_cast<const float4*>(&rowE[par][c0 + 4]);
+            const float inv = __frcp_rn(d);
+            float rsv[TC], rev[TC];
+#pragma unroll
+            for (int b4 = 0; b4 < TC; b4 += 4) {
+                const float4 sa = *reinterpret_cast<const float4*>(&rowS[par][c0 + b4]);
+                const float4 ea = *reinterpret_cast<const float4*>(&rowE[par][c0 + b4]);
+                rsv[b4] = sa.x; rsv[b4 + 1] = sa.y; rsv[b4 + 2] = sa.z; rsv[b4 + 3] = sa.w;
+                rev[b4] = ea.x; rev[b4 + 1] = ea.y; rev[b4 + 2] = ea.z; rev[b4 + 3] = ea.w;
+            }
             const float4 fr = *reinterpret_cast<const float4*>(&rowS[par][r0]);
-            const float rsv[TC] = {sa.x, sa.y, sa.z, sa.w, sb.x, sb.y, sb.z, sb.w};
-            const float rev[TC] = {ea.x, ea.y, ea.z, ea.w, eb.x, eb.y, eb.z, eb.w};
             const float fv[TR] = {fr.x, fr.y, fr.z, fr.w};
 #pragma unroll
             for (int a = 0; a < TR; ++a) {
@@ -233,7 +231,17 @@ __device__ void chol_inv_block(const float* G, int64_t ldg, int c, float* P, int
         }
         __syncthreads();
         if (!ok) {
-            shift = (shift == 0.0) ? 1e-6 * trace_s / c : shift * 1e3;
+            if (shift == 0.0) {   // first retry: the shift is relative to the trace of G
+                if (tid == 0) {
+                    double t = 0.0;
+                    for (int i = 0; i < c; ++i) t += double(G[int64_t(i) * ldg + i]);
+                    trace_s = t;
+                }
+                __syncthreads();
+                shift = 1e-6 * trace_s / c;
+            } else {
+                shift *= 1e3;
+            }
             if (tid == 0) atomicOr(shifted_flag, 1);
         }
     }
@@ -255,6 +263,17 @@ __device__ void chol_inv_block(const float* G, int64_t ldg, int c, float* P, int
             if (l < c) P[int64_t(i) * ldp + l] = (l <= i) ? e[a][b] * sc : 0.f;
         }
     }
+}
+
+// Block-wide device routine (all threads of the block call it; G and P may live in global
+// or shared memory): the 4 x 4 register tiling when the block has enough threads for it.
+__device__ void chol_inv_block(const float* G, int64_t ldg, int c, float* P, int64_t ldp, int* status,
+                               int* shifted_flag) {
+    const int n4 = (c + 3) / 4;
+    if (n4 * n4 <= int(blockDim.x))
+        chol_inv_block_t<4>(G, ldg, c, P, ldp, status, shifted_flag);
+    else
+        chol_inv_block_t<8>(G, ldg, c, P, ldp, status, shifted_flag);
 }
 
 __global__ void __launch_bounds__(512) chol_inv_tiled_kernel(const float* __restrict__ G, int64_t ldg, int c,
@@ -299,7 +318,8 @@ void cholqr_pass(Exec& ex, int64_t len, int64_t ld, const T* src, int c, T* dst,
     T* P = static_cast<T*>(ws.rfac);
     thin_mm<T>(ex, src, c, len, ld, false, c, src, ld, G, ws.ldp, false, ws);   // G = W^T W
     if (sizeof(T) == 4 && c <= 128) {
-        const int nthreads = ((c + TR - 1) / TR) * ((c + TC - 1) / TC);
+        const int n4 = (c + TR - 1) / TR;   // 4 x 4 tiles when they fit in 512 threads, else 4 x 8
+        const int nthreads = n4 * n4 <= 512 ? n4 * n4 : n4 * ((c + 7) / 8);
         chol_inv_tiled_kernel<<<1, (nthreads + 31) / 32 * 32, 0, ex.stream>>>(
             reinterpret_cast<const float*>(G), ws.ldp, c, reinterpret_cast<float*>(P), ws.ldp, ex.status,
             ws.shifted_flag);
@@ -723,7 +743,7 @@ __global__ void __launch_bounds__(NT, 1) orth_fused_kernel(Args a) {
         }
     }
     __syncthreads();
-    chol_inv_block(hbuf, c, c, pbuf, c, a.status, a.shifted_flag);
+    chol_inv_block_t<4>(hbuf, c, c, pbuf, c, a.status, a.shifted_flag);   // c <= 64 on 256 threads
     __syncthreads();
     // rows m .. m + c - 1 of coef (H, no longer needed) take P1^T; rows 0 .. m - 1 keep C2
     for (int e = tid; e < c * c; e += NT) {
@@ -753,7 +773,7 @@ __global__ void __launch_bounds__(NT, 1) orth_fused_kernel(Args a) {
     // ---- P4: Qout = P2 W1, P2 = chol(H3)^{-T}
     for (int e = tid; e < c * c; e += NT) hbuf[e] = __ldcg(a.gram + e);
     __syncthreads();
-    chol_inv_block(hbuf, c, c, pbuf, c, a.status, a.shifted_flag);
+    chol_inv_block_t<4>(hbuf, c, c, pbuf, c, a.status, a.shifted_flag);   // c <= 64 on 256 threads
     __syncthreads();
     for (int e = tid; e < c * c; e += NT) {
         const int b = e / c, j = e % c;
