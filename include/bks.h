@@ -241,14 +241,15 @@ bks_status bks_orthonormalize(bks_ctx* ctx, int dtype, int64_t len, int m, int c
 bks_status bks_sym_eig(bks_ctx* ctx, int dtype, int w, const void* M, int64_t ldm,
                        void* lam, void* U, int64_t ldu);
 
-/* ---- allocation-free variant ------------------------------------------------------ */
+/* ---- batches and differentiation ------------------------------------------------- */
 
 /* Block Krylov on a batch of independent matrices (As[0..batch), each dense or CSR, of
  * any shapes), the same k, q and opts for all: Zs[i] (n_i x k), sigmas[i] (k) and, if Vs
  * is non-NULL, Vs[i] (d_i x k), device buffers as for bks_block_krylov.  seeds[i] (NULL:
  * seed i) or pis[i] (NULL array, or NULL entries: generate from the seed) give the start
- * blocks.  The solves run on up to 8 streams of the context (created on first use), so
- * several are in flight at once; the batch is ordered after the work already on the
+ * blocks.  The solves run on up to 16 streams of the context (created on first use),
+ * launched from up to 8 host threads, so several are in flight at once; each result is
+ * that of the single solve.  The batch is ordered after the work already on the
  * context's stream, and later work on that stream after the batch.  statuses[i] (host,
  * may be NULL) receives each solve's status; the return value is the first error, else
  * BKS_WARN_DEFLATED if any solve was capped, else BKS_OK.  stats (may be NULL) sums
@@ -292,6 +293,8 @@ bks_status bks_backward(bks_ctx* ctx, int dtype, int64_t n, int64_t d, int k, in
  * context's stream. */
 bks_status bks_low_rank(bks_ctx* ctx, int dtype, int64_t n, int64_t d, int r, const void* U,
                         int64_t ldu, const void* sigma, const void* V, int64_t ldv, void* out);
+
+/* ---- allocation-free variant ------------------------------------------------------ */
 
 /* bks_sym_eig without any device allocation.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory when they call, for

@@ -48,6 +48,12 @@ struct KernelLog {
     }
 };
 
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum, once per
+// kernel and device (thread-safe); fails when `need` exceeds it.  A per-launch limit set to
+// each launch's own size would race between host threads that launch the same kernel
+// with different sizes (the limit is per function, not per launch).
+cudaError_t allow_dynamic_smem(const void* fn, size_t need);
+
 // Per-call launch bookkeeping.
 struct Exec {
     cudaStream_t stream = nullptr;

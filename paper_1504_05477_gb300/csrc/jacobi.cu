@@ -490,7 +490,7 @@ cudaError_t launch_cluster(cudaStream_t st, int C, size_t smem, const T* Xin, in
                            int b, T* X, int64_t ldw, int max_sweeps, T tol, int* status,
                            int* sweeps) {
     auto kern = jacobi_cluster_kernel<T, E, typename EngineFor<T, E>::type, DB>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t e = allow_dynamic_smem(reinterpret_cast<const void*>(kern), smem);
     if (e != cudaSuccess) return e;
     if (C > 8) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -571,8 +571,7 @@ void sym_eig(Exec& ex, int w, const T* Xin, int64_t ldx, T* X, int64_t ldw, T* l
         return;
     }
     const size_t lsmem = size_t(w) * sizeof(double);
-    if (lsmem > 48 * 1024)
-        cudaFuncSetAttribute(eig_rank_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(lsmem));
+    if (lsmem > 48 * 1024) allow_dynamic_smem(reinterpret_cast<const void*>(eig_rank_kernel<T>), lsmem);
     eig_rank_kernel<T><<<1, 1024, lsmem, ex.stream>>>(X, ldw, w, lam, order, nrm);
     eig_gather_kernel<T><<<w, 128, 0, ex.stream>>>(X, ldw, w, order, nrm, Vt, ldv);
     ex.launches += 2;

@@ -9,6 +9,8 @@
 // ensure), and W R^{-1} runs as a parallel GEMM.  A factorisation that meets a
 // non-positive pivot is retried with a growing diagonal shift (shifted CholeskyQR,
 // Fukaya et al. 2020); the status word records the shift.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace bks {
@@ -326,8 +328,7 @@ void cholqr_pass(Exec& ex, int64_t len, int64_t ld, const T* src, int c, T* dst,
     } else {
         const bool gj = size_t(2) * c * c * sizeof(T) <= 200 * 1024;
         const size_t smem = size_t(gj ? 2 : 1) * c * c * sizeof(T);
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(chol_inv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (smem > 48 * 1024) allow_dynamic_smem(reinterpret_cast<const void*>(chol_inv_kernel<T>), smem);
         chol_inv_kernel<T><<<1, 256, smem, ex.stream>>>(G, ws.ldp, c, P, ws.ldp, ex.status, ws.shifted_flag, gj);
     }
     ex.launches++;
@@ -805,26 +806,31 @@ bool orth_fused(Exec& ex, int64_t len, int64_t ld, const float* Qb, int m, float
                : tj == 16 ? reinterpret_cast<void*>(of::orth_fused_kernel<16>)
                : tj == 24 ? reinterpret_cast<void*>(of::orth_fused_kernel<24>)
                           : reinterpret_cast<void*>(of::orth_fused_kernel<32>);
+    static std::mutex mu;   // host threads of a batch may get here together
     static int configured_device[4] = {-1, -1, -1, -1};
     static int per_sm[4] = {0, 0, 0, 0};
     const int ti = tj / 8 - 1;
     int dev = 0;
     cudaGetDevice(&dev);
-    if (configured_device[ti] != dev) {
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(of::MAX_DYN_FLOATS * sizeof(float))) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[ti], fn, of::NT,
-                                                          of::MAX_DYN_FLOATS * sizeof(float)) != cudaSuccess) {
-            cudaGetLastError();
-            return false;
+    int resident = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (configured_device[ti] != dev) {
+            if (allow_dynamic_smem(fn, of::MAX_DYN_FLOATS * sizeof(float)) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[ti], fn, of::NT,
+                                                              of::MAX_DYN_FLOATS * sizeof(float)) != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+            configured_device[ti] = dev;
         }
-        configured_device[ti] = dev;
+        resident = per_sm[ti];
     }
     // about 64 rows per CTA: a short block takes only a few SMs (other streams keep the rest)
     int G = ex.num_sms < of::MAXG ? ex.num_sms : of::MAXG;
     const int64_t want = (len + 63) / 64;
     if (want < G) G = int(want < 1 ? 1 : want);
-    if (per_sm[ti] < 1 || int64_t(G) * of::r4((m + c) * c) > ws.fpart_cap) return false;
+    if (resident < 1 || int64_t(G) * of::r4((m + c) * c) > ws.fpart_cap) return false;
     of::Args a;
     a.Q = Qb; a.W = W; a.Wtmp = Wtmp; a.Qout = Qout;
     a.m = m; a.c = c; a.len = len; a.ld = ld;

@@ -11,7 +11,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/bks.h"
@@ -54,7 +56,8 @@ struct bks_ctx {
 namespace {
 
 constexpr int BKS_VERSION = 100;
-constexpr int BKS_BATCH_STREAMS = 8;   // solves of a batch in flight at once
+constexpr int BKS_BATCH_THREADS = 8;   // host threads issuing the solves of a batch
+constexpr int BKS_BATCH_STREAMS = 16;  // solves of a batch in flight at once (two per thread)
 
 struct Arena {
     size_t off = 0;
@@ -832,6 +835,33 @@ bks_status solve_entry(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t
 
 namespace bks {
 
+cudaError_t allow_dynamic_smem(const void* fn, size_t need) {
+    struct Entry {
+        const void* fn;
+        int dev;
+        int limit;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> done;
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const Entry& e : done)
+        if (e.fn == fn && e.dev == dev) return size_t(e.limit) >= need ? cudaSuccess : cudaErrorInvalidValue;
+    cudaFuncAttributes fa;
+    err = cudaFuncGetAttributes(&fa, fn);
+    if (err != cudaSuccess) return err;
+    int optin = 0;
+    err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (err != cudaSuccess) return err;
+    const int limit = optin - int(fa.sharedSizeBytes);
+    err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit);
+    if (err != cudaSuccess) return err;
+    done.push_back(Entry{fn, dev, limit});
+    return size_t(limit) >= need ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 int ctx_num_sms(const bks_ctx* ctx) { return ctx->num_sms; }
 
 bks_status ctx_workspace(bks_ctx* ctx, size_t bytes, CtxInfo* info) {
@@ -1029,7 +1059,6 @@ bks_status bks_block_krylov_batched(bks_ctx* ctx, int batch, const bks_matrix* A
     cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
     cudaEventRecord(start, ctx->stream);
     for (int j = 0; j < S; ++j) cudaStreamWaitEvent(ctx->subs[j]->stream, start, 0);
-    std::vector<int> owner(S, -1);
     bks_status worst = BKS_OK;
     auto note = [&](int i, bks_status st_i, const bks_stats& one) {
         if (statuses) statuses[i] = st_i;
@@ -1046,21 +1075,44 @@ bks_status bks_block_krylov_batched(bks_ctx* ctx, int batch, const bks_matrix* A
             stats->product_flops += one.product_flops;
         }
     };
-    for (int i = 0; i < batch; ++i) {
-        bks_ctx* sub = ctx->subs[i % S];
-        bks_stats one{};
-        if (owner[i % S] >= 0) note(owner[i % S], finish_solve(sub, &one), one);
-        owner[i % S] = -1;
-        one = bks_stats{};
-        const bks_status st_i = solve_entry(sub, &As[i], k, q, seeds ? seeds[i] : uint64_t(i),
-                                            pis ? pis[i] : nullptr, Zs[i], sigmas[i], Vs ? Vs[i] : nullptr, opts,
-                                            nullptr, true, false, true);
-        if (sub->pending.active) owner[i % S] = i;
-        else note(i, st_i, one);
+    // T host threads issue the launches in parallel (a solve is a few dozen short kernels,
+    // so one thread cannot keep the GPU busy): thread t takes matrices t, t + T, ... and
+    // alternates between its stream contexts t and t + T, finishing the older solve on a
+    // context before it reuses it.  Every solve is independent, so the results are those
+    // of single solves, whatever the threads' timing.
+    const int T = S < BKS_BATCH_THREADS ? S : BKS_BATCH_THREADS;
+    std::vector<bks_status> st_all(size_t(batch), BKS_OK);
+    std::vector<bks_stats> one_all(static_cast<size_t>(batch));
+    auto worker = [&](int t) {
+        DeviceGuard gd(ctx->device);
+        int owner[2] = {-1, -1};
+        bks_ctx* subs[2] = {ctx->subs[t], ctx->subs[t + T < S ? t + T : t]};
+        int r = 0;
+        for (int i = t; i < batch; i += T, ++r) {
+            const int h = r & 1;
+            bks_ctx* sub = subs[h];
+            if (owner[h] >= 0) st_all[owner[h]] = finish_solve(sub, &one_all[owner[h]]);
+            owner[h] = -1;
+            const bks_status st_i = solve_entry(sub, &As[i], k, q, seeds ? seeds[i] : uint64_t(i),
+                                                pis ? pis[i] : nullptr, Zs[i], sigmas[i], Vs ? Vs[i] : nullptr,
+                                                opts, nullptr, true, false, true);
+            if (sub->pending.active) owner[h] = i;
+            else st_all[i] = st_i;
+        }
+        for (int h = 0; h < 2; ++h)
+            if (owner[h] >= 0) st_all[owner[h]] = finish_solve(subs[h], &one_all[owner[h]]);
+    };
+    std::vector<std::thread> threads;
+    int started = 0;   // threads 1 .. started run concurrently; the rest run here
+    try {
+        for (int t = 1; t < T; ++t, ++started) threads.emplace_back(worker, t);
+    } catch (...) {
     }
+    worker(0);
+    for (int t = started + 1; t < T; ++t) worker(t);
+    for (std::thread& th : threads) th.join();
+    for (int i = 0; i < batch; ++i) note(i, st_all[i], one_all[i]);
     for (int j = 0; j < S; ++j) {
-        bks_stats one{};
-        if (owner[j] >= 0) note(owner[j], finish_solve(ctx->subs[j], &one), one);
         // later work on the caller's stream is ordered after the batch
         cudaEventRecord(start, ctx->subs[j]->stream);
         cudaStreamWaitEvent(ctx->stream, start, 0);

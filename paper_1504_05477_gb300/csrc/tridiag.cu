@@ -596,7 +596,7 @@ template <typename T>
 bool reduce_and_bisect(Exec& ex, int w, const T* M, int m, T* scratch, const TdScratch& L) {
     const TdShape sh = td_pick<T>(w);
     auto kern = tridiag_kernel<T>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sh.smem)) != cudaSuccess ||
+    if (allow_dynamic_smem(reinterpret_cast<const void*>(kern), sh.smem) != cudaSuccess ||
         (sh.C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
         cudaGetLastError();
         return false;
@@ -654,8 +654,7 @@ bool topk_tridiag(Exec& ex, int w, const T* M, int m, T* Vt, int64_t ldv, T* scr
     if (!reduce_and_bisect(ex, w, M, m, scratch, L)) return false;
     const int vpc = invit_vpc<T>(w);
     const size_t ismem = invit_smem<T>(w, vpc);
-    if (ismem > 48 * 1024)
-        cudaFuncSetAttribute(invit_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ismem));
+    if (ismem > 48 * 1024) allow_dynamic_smem(reinterpret_cast<const void*>(invit_kernel<T>), ismem);
     invit_kernel<T><<<(m + vpc - 1) / vpc, vpc, ismem, ex.stream>>>(dT, eT, lam, tn, w, m, X, ldx, ex.status);
     ex.launches += 1;
     // orthonormal eigenvector basis (CholeskyQR2 of the m x w block; thin blocks keep
@@ -665,12 +664,10 @@ bool topk_tridiag(Exec& ex, int w, const T* M, int m, T* Vt, int64_t ldv, T* scr
     const int nref = w - 2;
     const int nblk = (nref + WY_NB - 1) / WY_NB;
     const size_t fsmem = size_t(WY_NB) * round_up(w, 4) * sizeof(T);
-    if (fsmem > 48 * 1024)
-        cudaFuncSetAttribute(wy_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(fsmem));
+    if (fsmem > 48 * 1024) allow_dynamic_smem(reinterpret_cast<const void*>(wy_factor_kernel<T>), fsmem);
     wy_factor_kernel<T><<<nblk, 256, fsmem, ex.stream>>>(V, tau, w, nref, Tw);
     const size_t asmem = wy_apply_smem<T>(w);
-    if (asmem > 48 * 1024)
-        cudaFuncSetAttribute(wy_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(asmem));
+    if (asmem > 48 * 1024) allow_dynamic_smem(reinterpret_cast<const void*>(wy_apply_kernel<T>), asmem);
     wy_apply_kernel<T><<<(m + WY_WARPS - 1) / WY_WARPS, WY_WARPS * 32, asmem, ex.stream>>>(X, ldx, w, m, nref, V,
                                                                                            Tw, Vt, ldv);
     ex.launches += 2;
