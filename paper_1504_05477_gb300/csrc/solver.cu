@@ -16,9 +16,17 @@
 #include <thread>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/bks.h"
 #include "common.cuh"
 #include "ctx.cuh"
+
+namespace bks {
+namespace tc {
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn();   // tensor-core products: looked up on first use
+}
+}  // namespace bks
 
 
 using namespace bks;
@@ -1102,6 +1110,7 @@ bks_status bks_block_krylov_batched(bks_ctx* ctx, int batch, const bks_matrix* A
         for (int h = 0; h < 2; ++h)
             if (owner[h] >= 0) st_all[owner[h]] = finish_solve(subs[h], &one_all[owner[h]]);
     };
+    tc::encode_fn();   // the tensor-map encoder's one-time lookup, before the threads start
     std::vector<std::thread> threads;
     int started = 0;   // threads 1 .. started run concurrently; the rest run here
     try {

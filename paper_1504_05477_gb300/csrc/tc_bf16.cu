@@ -259,7 +259,8 @@ size_t smem_bytes() {
 template <int CP, int NP>
 cudaError_t launch(Exec& ex, const CUtensorMap& tmA, const CUtensorMap& tmX, const Params& p, int G) {
     const size_t smem = smem_bytes<CP, NP>();
-    cudaError_t err = allow_dynamic_smem(reinterpret_cast<const void*>(bf16_product_kernel<CP, NP>), smem);
+    cudaError_t err = cudaFuncSetAttribute(bf16_product_kernel<CP, NP>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (err != cudaSuccess) return err;
     // the kernel log times the HBM-bound products (X rounded to BF16) only
     KernelLog* log = NP == 1 ? ex.klog : nullptr;

@@ -504,17 +504,19 @@ __global__ void tf32_split_kernel(const float* __restrict__ x, int rows, int64_t
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    // looked up once; the initialisation of a function-local static is thread-safe
-    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
         void* ptr = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
                                              &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
-        cudaGetLastError();
-        return nullptr;
-    }();
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+        else
+            cudaGetLastError();
+    }
     return fn;
 }
 
@@ -631,7 +633,8 @@ bool tc_product_f32(Exec& ex, const float* A, int64_t n, int64_t d, int64_t lda,
         switch (cp) {
 #define BKS_TC(CPV)                                                                         \
     case CPV:                                                                               \
-        err = allow_dynamic_smem(reinterpret_cast<const void*>(tc_product_kernel<CPV>), smem); \
+        err = cudaFuncSetAttribute(tc_product_kernel<CPV>,                                  \
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)); \
         if (err == cudaSuccess) {                                                           \
             if (ex.klog) ex.klog->record(ex.stream);                                        \
             tc_product_kernel<CPV><<<Gc, NTHREADS, smem, ex.stream>>>(tmA, tmXh, tmXl, p);  \
