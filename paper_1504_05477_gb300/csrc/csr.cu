@@ -270,17 +270,10 @@ __global__ void spmm_seg_kernel(const int64_t* __restrict__ row_ptr, const int32
 __global__ void spmm_fixup_kernel(const int64_t* __restrict__ seg_off, int64_t rows,
                                   const float* __restrict__ part, int c, int xp, float* __restrict__ out,
                                   int corr_kind, const double* __restrict__ cvec, const float* __restrict__ mu) {
-    // element e = r c + j; (r, j) advance by the grid stride without a division per element
-    const int64_t e0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x, stride = int64_t(gridDim.x) * blockDim.x;
-    const int64_t sr = stride / c;
-    const int sj = int(stride % c);
-    int64_t r = e0 / c;
-    int j = int(e0 % c);
-    for (int64_t e = e0; e < rows * c; e += stride, r += sr, j += sj) {
-        if (j >= c) {
-            j -= c;
-            ++r;
-        }
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < rows * c;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t r = e / c;
+        const int j = int(e % c);
         const int64_t s0 = seg_off[r], s1 = seg_off[r + 1];
         if (s1 - s0 <= 1) continue;
         double acc = 0.0;
