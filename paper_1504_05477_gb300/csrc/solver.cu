@@ -1097,7 +1097,7 @@ bks_status bks_block_krylov_batched(bks_ctx* ctx, int batch, const bks_matrix* A
         bks_ctx* subs[2] = {ctx->subs[t], ctx->subs[t + T < S ? t + T : t]};
         int r = 0;
         for (int i = t; i < batch; i += T, ++r) {
-            const int h = r & 1;
+            const int h = subs[1] == subs[0] ? 0 : (r & 1);   // one context: finish before reuse
             bks_ctx* sub = subs[h];
             if (owner[h] >= 0) st_all[owner[h]] = finish_solve(sub, &one_all[owner[h]]);
             owner[h] = -1;
