@@ -37,7 +37,7 @@ typedef enum {
     BKS_ERR_BREAKDOWN = 5,      /* Cholesky of a Gram matrix failed even after shifting */
     BKS_ERR_NOT_CONVERGED = 6,  /* Jacobi eigen-solver hit its sweep cap */
     BKS_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up */
-    BKS_ERR_UNSUPPORTED = 8,    /* valid request this build does not implement */
+    BKS_ERR_UNSUPPORTED = 8,    /* valid request the library does not implement */
     BKS_WARN_DEFLATED = 100     /* results valid; q was capped or Krylov columns were dependent */
 } bks_status;
 
