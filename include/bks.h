@@ -237,7 +237,8 @@ bks_status bks_orthonormalize(bks_ctx* ctx, int dtype, int64_t len, int m, int c
 /* Eigen-decomposition of a symmetric positive semi-definite w x w matrix M (row-major,
  * ldm) by one-sided Jacobi (Alg. 2 step 5: the top singular vectors of M are its top
  * eigenvectors).  lam: out, w eigenvalues, descending.  U: out, w x w row-major,
- * column i the eigenvector of lam[i].  FP32 or FP64 (dtype). */
+ * column i the eigenvector of lam[i].  FP32 or FP64 (dtype).  Non-finite entries of M
+ * are not detected: the results are then undefined (or BKS_ERR_NOT_CONVERGED). */
 bks_status bks_sym_eig(bks_ctx* ctx, int dtype, int w, const void* M, int64_t ldm,
                        void* lam, void* U, int64_t ldu);
 
@@ -316,7 +317,10 @@ bks_status bks_low_rank(bks_ctx* ctx, int dtype, int64_t n, int64_t d, int r, co
  * before any stream capture.  Every call shares the one array, which keeps the
  * previous call's contents (the status words are cleared at the start of each call):
  * calls whose work overlaps on the GPU (other streams, other host threads) race on it
- * and must be serialised by the caller.  Errors are returned as status codes only
+ * and must be serialised by the caller.  The address looked up on the first call is
+ * kept for the life of the process: it assumes the device's primary context (the one
+ * the CUDA runtime uses) and no cudaDeviceReset in between.  As for bks_sym_eig,
+ * non-finite entries of M are not detected.  Errors are returned as status codes only
  * (there is no context for bks_last_error). */
 #define BKS_NOALLOC_EIG_MAX_W 512
 bks_status bks_sym_eig_noalloc(void* stream, int dtype, int w, const void* M, int64_t ldm,

@@ -17,14 +17,26 @@ namespace bks {
 namespace {
 
 // Scratch of the no-allocation eigen-solve: X (w x w), Vt (w x w), column norms,
-// order and the status words.  5 MiB covers w <= BKS_NOALLOC_EIG_MAX_W in FP32 and FP64.
+// order and the status words, each 256-byte aligned.  5 MiB covers w <=
+// BKS_NOALLOC_EIG_MAX_W in FP32 and FP64 (the static_assert below checks the FP64 case).
+constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+struct ScratchLayout {
+    size_t x, nrm, vt, ord, stat, total;
+    constexpr ScratchLayout(int w, size_t tb)
+        : x(0),
+          nrm(align256(size_t(w) * w * tb)),
+          vt(nrm + align256(size_t(w) * tb)),
+          ord(vt + align256(size_t(w) * w * tb)),
+          stat(ord + align256(size_t(w) * 4)),
+          total(stat + 256) {}
+};
 constexpr size_t kScratchBytes = size_t(5) << 20;
+static_assert(ScratchLayout(BKS_NOALLOC_EIG_MAX_W, 8).total <= kScratchBytes,
+              "the static scratch must hold the FP64 layout at the largest supported width");
 static __device__ __align__(256) unsigned char g_eig_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 void* g_scratch_ptr[kMaxDevices];   // device address of g_eig_scratch, per device
-
-size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 }  // namespace
 }  // namespace bks
@@ -40,10 +52,9 @@ extern "C" bks_status bks_sym_eig_noalloc(void* stream, int dtype, int w, const 
     int C, b, E;
     size_t smem;
     if (!jacobi_plan(w, int(tb), C, b, E, smem)) return BKS_ERR_UNSUPPORTED;
-    const size_t o_x = 0, o_nrm = o_x + align256(size_t(w) * w * tb),
-                 o_vt = o_nrm + align256(size_t(w) * tb), o_ord = o_vt + align256(size_t(w) * w * tb),
-                 o_stat = o_ord + align256(size_t(w) * 4), total = o_stat + 256;
-    if (total > kScratchBytes) return BKS_ERR_INVALID_ARG;
+    const ScratchLayout lay(w, tb);
+    const size_t o_x = lay.x, o_nrm = lay.nrm, o_vt = lay.vt, o_ord = lay.ord, o_stat = lay.stat;
+    if (lay.total > kScratchBytes) return BKS_ERR_INVALID_ARG;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -87,7 +98,6 @@ extern "C" bks_status bks_sym_eig_noalloc(void* stream, int dtype, int w, const 
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return BKS_ERR_CUDA;
-    if (words[0] & ST_NONFINITE) return BKS_ERR_NONFINITE;
     if (words[0] & ST_NOT_CONVERGED) return BKS_ERR_NOT_CONVERGED;
     if (words[1] < 0) return BKS_ERR_UNSUPPORTED;
     return BKS_OK;
