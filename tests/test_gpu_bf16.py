@@ -6,8 +6,15 @@ Tolerances.  Exact products (three BF16 pieces of X) carry only FP32 accumulatio
 |Y - Y_ref| <= 4 sqrt(K) eps32 (|A| |X|).  BF16-mode products are compared with the
 FP64 product of A and X rounded to BF16 (the operands the tensor cores see), to the same
 bound.  The solve in "f32" precision on a BF16 A follows the FP32 bar (relative sigma
-1e-5); the BF16 mode is held to relative sigma 1e-3 with refinement and 1e-2 without,
-and to error ratios within 1e-3 of the oracle's with refinement."""
+1e-5).  The BF16 mode rounds the thin operands of the Krylov products to BF16, so its
+basis is not the oracle's; the refinement recomputes B = A^T Q FP32-accurately on that
+basis.  For Block Krylov the leading Ritz values are converged directions of a wide
+space, which a perturbation of the basis moves only at second order: relative sigma 1e-5
+with refinement, 3e-4 without (measured 1.3e-4 at width 100).  Simultaneous Iteration's
+k-dimensional space is far from converged at q = 4 on the slowly decaying i^-1/2
+spectrum, and the BF16 rounding of its iterates moves the Ritz values at first order:
+1e-3 in both forms (measured 1.3e-4 and 3.4e-4 with refinement).  Every form keeps the
+error ratios within 1e-3 of the oracle's."""
 import numpy as np
 import pytest
 
@@ -99,22 +106,27 @@ def _planted(m, d, seed):
 
 
 @pytest.mark.parametrize("method", ["bki", "si"])
-def test_bf16_solve_small_parity(method):
-    m, d, k, q = 2048, 1024, 20, 4
-    a, a64 = _planted(m, d, 41)
+@pytest.mark.parametrize("m,d,k,q", [(2048, 1024, 20, 4), (4096, 2048, 32, 4)])
+def test_bf16_solve_small_parity(method, m, d, k, q):
+    """Width 100 and 160 (Block Krylov): the refinement of B = A^T Q then runs on one and
+    on two groups of 128 columns."""
+    a, a64 = _planted(m, d, 41 + m)
     pi = synth.gaussian_pi(4, d, k)
     ref = (krylov.block_krylov if method == "bki" else krylov.simul_iter)(a64, k, q, pi)
     sig = metrics.true_singular_values(a64)
     r_ora = metrics.ratios(a64, ref.Z, k, sigma=sig)
     fn = bk.block_krylov if method == "bki" else bk.simul_iter
+    bki = method == "bki"
     cases = {"f32": (dict(precision="f32"), 1e-5, 1e-3),
-             "bf16_refined": (dict(precision="bf16"), 1e-3, 1e-3),
-             "bf16_plain": (dict(precision="bf16", refine=False), 1e-2, 2e-2)}
+             "bf16_refined": (dict(precision="bf16"), 1e-5 if bki else 1e-3, 1e-3),
+             "bf16_plain": (dict(precision="bf16", refine=False), 3e-4 if bki else 1e-3, 1e-3)}
     for name, (kw, s_tol, r_tol) in cases.items():
         z, s = fn(a, k, q, pi=dev(pi), **kw)
         z, s = host(z), host(s)
-        assert np.max(np.abs(s - ref.sigma) / ref.sigma) <= s_tol, name
-        assert np.max(np.abs(z.T @ z - np.eye(k))) < 1e-4, name
+        rel = np.max(np.abs(s - ref.sigma) / ref.sigma)
+        assert rel <= s_tol, (name, rel)
+        orth = np.max(np.abs(z.T @ z - np.eye(k)))
+        assert orth < 1e-5, (name, orth)
         r = metrics.ratios(a64, z, k, sigma=sig)
         for key in r:
             assert abs(r[key] - r_ora[key]) <= r_tol, (name, key, r[key], r_ora[key])

@@ -273,44 +273,12 @@ def test_nonfinite_input_reported():
     a[17, 3] = np.nan
     with pytest.raises(bk.BksError) as e:
         bk.block_krylov(dev(a), 5, 2)
-    assert e.value.status in (4, 5)
+    assert e.value.status == 4   # BKS_ERR_NONFINITE: the NaN reaches the first Gram matrix
+    # the context stays usable
+    a[17, 3] = 1.0
+    z, s = bk.block_krylov(dev(a), 5, 2)
+    assert bool(torch.isfinite(s).all())
 
 
 # ------------------------------------------------------------- full size 20000 x 8000
-@pytest.fixture(scope="module")
-def noisy_full():
-    a, _ = synth.dense_planted_noisy()
-    return a
-
-
-def _true_sigma_top(a64, k_extra=80):
-    """Reference singular values: the oracle's own BKI at a large width (its Ritz values
-    converge from below, Sec. 6), enough for sigma_1..sigma_{k+1}."""
-    pi = synth.gaussian_pi(99, a64.shape[1], k_extra)
-    return krylov.block_krylov(a64, k_extra, 12, pi).sigma
-
-
-def test_full_size_block_krylov_parity(noisy_full):
-    a = noisy_full
-    k, q = 50, 8
-    pi = synth.gaussian_pi(2, 8000, k)
-    z, s = bk.block_krylov(dev(a), k, q, pi=dev(pi))
-    z, s = host(z).astype(np.float64), host(s).astype(np.float64)
-    a64 = a.astype(np.float64)
-    ref = krylov.block_krylov(a64, k, q, pi)
-    assert np.max(np.abs(s - ref.sigma) / ref.sigma) <= 1e-5
-    assert np.max(np.abs(z.T @ z - np.eye(k))) < 1e-4
-    # Frobenius and per-vector ratios need only Z^T A and the reference sigma
-    st = _true_sigma_top(a64)
-    fro_a = np.sum(a64 * a64)
-    tail = fro_a - np.sum(st[:k] ** 2)
-    for zz in (z, ref.Z):
-        zta = zz.T @ a64
-        cap = np.einsum("ij,ij->i", zta, zta)
-        zz_pv = np.max(np.abs(st[:k] ** 2 - cap)) / st[k] ** 2
-        zz_fr = np.sqrt(max(fro_a - cap.sum(), 0.0) / tail)
-        if zz is z:
-            g = (zz_pv, zz_fr)
-        else:
-            o = (zz_pv, zz_fr)
-    assert abs(g[0] - o[0]) <= 1e-3 and abs(g[1] - o[1]) <= 1e-3
+# The full-size 20000 x 8000 parity test lives in test_gpu_fullsize.py.

@@ -75,15 +75,19 @@ def test_sparse_products(centred, trans):
     x64 = x.astype(np.float64)
     ref = m @ x64
     absd = abs(m) @ np.abs(x64)
+    corr = np.zeros_like(ref)
     if centred:
         mu64 = mu.astype(np.float64)
         if trans:
-            ref = ref - np.outer(mu64, x64.sum(axis=0))
+            corr = np.outer(mu64, x64.sum(axis=0))
         else:
-            ref = ref - np.outer(np.ones(n), mu64 @ x64)
+            corr = np.outer(np.ones(n), mu64 @ x64)
+        ref = ref - corr
+    # element-wise: FP32 accumulation of a row's lmax products, the correction (summed in
+    # FP64 on the device) rounded once to FP32 and subtracted, the result rounded once
     lmax = np.max(np.diff(m.tocsr().indptr))
-    bound = 4 * np.sqrt(lmax) * EPS32 * absd + 1e-6 * np.max(np.abs(ref))
-    assert np.all(np.abs(y - ref) <= bound)
+    bound = 4 * np.sqrt(lmax) * EPS32 * absd + 2 * EPS32 * np.abs(corr) + 2 * EPS32 * np.abs(ref) + 1e-38
+    assert np.all(np.abs(y - ref) <= bound), float(np.max(np.abs(y - ref) / bound))
 
 
 @pytest.mark.parametrize("method", ["bki", "si"])
@@ -98,7 +102,7 @@ def test_sparse_centred_small_parity(method):
     op = krylov.centred_csr_op(row_ptr, col_idx, vals, n, d, mu)
     ref = (krylov.block_krylov if method == "bki" else krylov.simul_iter)(op, k, q, pi)
     assert np.max(np.abs(s - ref.sigma) / ref.sigma) <= 1e-5
-    assert np.max(np.abs(z.T @ z - np.eye(k))) < 1e-4
+    assert np.max(np.abs(z.T @ z - np.eye(k))) < 1e-5, np.max(np.abs(z.T @ z - np.eye(k)))
     dense = op.dense()
     sig = metrics.true_singular_values(dense)
     r_gpu = metrics.ratios(dense, z, k, sigma=sig)
@@ -121,7 +125,7 @@ def test_sparse_centred_full_size_parity():
     ref = krylov.block_krylov(op, k, q, pi)
     assert np.max(np.abs(s - ref.sigma) / ref.sigma) <= 1e-5
     zz = host(z).astype(np.float64)
-    assert np.max(np.abs(zz.T @ zz - np.eye(k))) < 1e-4
+    assert np.max(np.abs(zz.T @ zz - np.eye(k))) < 1e-5, np.max(np.abs(zz.T @ zz - np.eye(k)))
     # per-vector captured variance agrees with the oracle's (Z^T A_c through the operator)
     cap_g = np.sum(op.tmul(zz) ** 2, axis=0)
     cap_o = np.sum(op.tmul(ref.Z) ** 2, axis=0)
@@ -192,4 +196,4 @@ def test_graph_adjacency_centred_parity(method):
     op = krylov.centred_csr_op(row_ptr, col_idx, vals, n, n, mu)
     ref = (krylov.block_krylov if method == "bki" else krylov.simul_iter)(op, k, q, pi)
     assert np.max(np.abs(s - ref.sigma) / ref.sigma) <= 1e-5
-    assert np.max(np.abs(z.T @ z - np.eye(k))) < 1e-4
+    assert np.max(np.abs(z.T @ z - np.eye(k))) < 1e-5, np.max(np.abs(z.T @ z - np.eye(k)))
