@@ -164,15 +164,39 @@ struct OrthWs {
     int64_t fpart_cap = 0;        //   Grams (floats), the reduced Gram and the barrier words
     float* fgram = nullptr;
     unsigned* fbar = nullptr;
+    // tensor-core kernel (FP32; otc_part == nullptr disables it): partial Grams, the
+    // coefficient tiles (128 x otc_ldct), the reduced c x c Gram and the barrier words
+    float* otc_part = nullptr;
+    int64_t otc_cap = 0;
+    float* otc_cts = nullptr;
+    int64_t otc_ldct = 0;
+    float* otc_h = nullptr;
+    unsigned* otc_bar = nullptr;
+    // row-major copy of the m earlier columns (len x ldr); the call appends its output
+    // block at columns [m, m + c).  nullptr: only m = 0 runs on the tensor-core kernel
+    float* qr = nullptr;
+    int64_t ldr = 0;
+    bool qr_append = false;       // write the output block into qr at columns [m, m + c)
+    bool* tc_used = nullptr;      // host flag: set to whether the tensor-core kernel ran
 };
 // Byte sizes of those buffers for blocks of c columns, at most mmax earlier columns and
 // lengths up to len_max (pitch up to ld_max).
 struct OrthSizes {
-    size_t partials, g, rfac, ct, xh, tpart, fpart, fgram, fbar;
+    size_t partials, g, rfac, ct, xh, tpart, fpart, fgram, fbar, otc_part, otc_cts, otc_h, otc_bar;
     int ldp;
-    int64_t ldc, cap, tcap, fcap;
+    int64_t ldc, cap, tcap, fcap, otc_cap, otc_ldct;
 };
 OrthSizes orth_sizes(int64_t len_max, int64_t ld_max, int mmax, int c, int elem_bytes, bool tc, int num_sms);
+
+// Tensor-core block orthonormalisation (orth_tc.cu): W (c x ld) against Qc (m x ld) and its
+// row-major copy Qr (len x ldr; may be nullptr when m = 0), result in Qout and, when Qr_out
+// is non-null, row-major at Qr_out (pitch ldr).  False, launching nothing, when the
+// shapes do not fit.
+bool orth_tc_fits(int64_t len, int m, int c, int num_sms);
+size_t orth_tc_part_floats(int64_t len, int mmax, int c, int num_sms);
+bool orth_tc(Exec& ex, int64_t len, int64_t ld, const float* Qc, int m, const float* W, int c, float* Qout,
+             const float* Qr, float* Qr_out, int64_t ldr, float* part, int64_t part_cap, float* cts, int64_t ldct,
+             float* hbuf, unsigned* bar, int* shifted_flag);
 
 // Block orthonormalisation: W (c x ld thin) against Qb (m x ld thin), BCGS2 then
 // CholeskyQR2, result in Qout (may equal W); Wtmp: c x ld scratch.

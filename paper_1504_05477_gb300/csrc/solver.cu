@@ -302,8 +302,8 @@ struct Plan {
     CsrLayout csr;
     size_t td, td_bytes;     // scratch of the tridiagonal eigen-solve (0 bytes when it cannot run)
     size_t Qt, Bt, QBt, Pit, W, Wtmp, Wb, Wbtmp, part, og, rfac, ct, Rm, JX, lam, nrm, Vt,
-        order, Vk, stat, fpart, fgram, fbar;
-    int64_t fcap;
+        order, Vk, stat, fpart, fgram, fbar, otc_part, otc_cts, otc_h, otc_bar, qr;
+    int64_t fcap, otc_cap, otc_ldct, ldr;
     int ldp;
     int64_t ldc;
     int64_t part_cap;
@@ -355,6 +355,16 @@ Plan make_plan(const bks_matrix* A, int k, int q_eff, int w, size_t tb, int sms,
     p.fpart = a.take(size_t(p.fcap) * 4);
     p.fgram = a.take(on.fgram > od.fgram ? on.fgram : od.fgram);
     p.fbar = a.take(16);
+    // tensor-core orthonormalisation of the n-space blocks (FP32): its scratch and the
+    // row-major copy of Q it reads the updates from
+    p.otc_cap = on.otc_cap;
+    p.otc_ldct = on.otc_ldct;
+    p.otc_part = a.take(on.otc_part);
+    p.otc_cts = a.take(on.otc_cts);
+    p.otc_h = a.take(on.otc_h);
+    p.otc_bar = a.take(on.otc_bar);
+    p.ldr = round_up(w, 32);
+    p.qr = a.take(on.otc_part > 0 ? size_t(n) * p.ldr * 4 : 0);
     p.Rm = a.take(size_t(w) * w * tb);
     p.JX = a.take(size_t(w) * w * tb);
     p.lam = a.take(size_t(w) * tb);
@@ -584,10 +594,34 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
             ows.fgram = reinterpret_cast<float*>(base + p.fgram);
             ows.fbar = reinterpret_cast<unsigned*>(base + p.fbar);
         }
+        if (p.otc_cap > 0) {                         // tensor-core orthonormalisation
+            ows.otc_part = reinterpret_cast<float*>(base + p.otc_part);
+            ows.otc_cap = p.otc_cap;
+            ows.otc_cts = reinterpret_cast<float*>(base + p.otc_cts);
+            ows.otc_ldct = p.otc_ldct;
+            ows.otc_h = reinterpret_cast<float*>(base + p.otc_h);
+            ows.otc_bar = reinterpret_cast<unsigned*>(base + p.otc_bar);
+        }
     }
+    // Krylov blocks on the tensor-core kernel keep a row-major copy of Q (columns appended
+    // block by block); once a block falls back to the CUDA-core kernel the copy is
+    // incomplete and the later blocks stay on the CUDA cores
+    bool qr_ok = krylov && p.otc_cap > 0;
+    bool tc_ran = false;
     auto orth = [&](int m, T* Qout) {
         const int b = prof.begin();
+        if (qr_ok) {
+            ows.qr = reinterpret_cast<float*>(base + p.qr);
+            ows.ldr = p.ldr;
+            ows.qr_append = true;
+            ows.tc_used = &tc_ran;
+        }
         orth_block<T>(ex, n, p.ldn, Qt, m, W, k, Wtmp, Qout, ows);
+        if (qr_ok && !tc_ran) qr_ok = false;
+        ows.qr = nullptr;
+        ows.ldr = 0;
+        ows.qr_append = false;
+        ows.tc_used = nullptr;
         prof.end(1, b);
     };
     // QR of the kept blocks B_i in d-space (R = Q_B^T B preconditions the eigen-solve)
@@ -1267,7 +1301,13 @@ bks_status bks_orthonormalize(bks_ctx* ctx, int dtype, int64_t len, int m, int c
     const size_t o_part = a.take(z.partials), o_g = a.take(z.g), o_rfac = a.take(z.rfac),
                  o_ct = a.take(z.ct), o_xh = a.take(z.xh), o_xl = a.take(z.xh), o_tp = a.take(z.tpart),
                  o_fp = a.take(z.fpart), o_fg = a.take(z.fgram), o_fb = a.take(z.fbar),
-                 o_wtmp = a.take(size_t(c) * ldw * tb), o_stat = a.take(16);
+                 o_wtmp = a.take(size_t(c) * ldw * tb), o_stat = a.take(16),
+                 o_op = a.take(z.otc_part), o_oc = a.take(z.otc_cts), o_oh = a.take(z.otc_h),
+                 o_ob = a.take(z.otc_bar);
+    // the tensor-core kernel reads the updates from a row-major copy of Qb
+    const int64_t ldr = round_up(m > 0 ? m : 1, 32);
+    const bool otc = tc && z.otc_cap > 0 && orth_tc_fits(len, m, c, ctx->num_sms);
+    const size_t o_qr = a.take(otc && m > 0 ? size_t(len) * ldr * 4 : 0);
     bks_status s = ensure_ws(ctx, a.off);
     if (s != BKS_OK) return s;
     char* base = static_cast<char*>(ctx->ws);
@@ -1295,6 +1335,19 @@ bks_status bks_orthonormalize(bks_ctx* ctx, int dtype, int64_t len, int m, int c
         ws.fpart_cap = z.fcap;
         ws.fgram = reinterpret_cast<float*>(base + o_fg);
         ws.fbar = reinterpret_cast<unsigned*>(base + o_fb);
+    }
+    if (otc) {
+        ws.otc_part = reinterpret_cast<float*>(base + o_op);
+        ws.otc_cap = z.otc_cap;
+        ws.otc_cts = reinterpret_cast<float*>(base + o_oc);
+        ws.otc_ldct = z.otc_ldct;
+        ws.otc_h = reinterpret_cast<float*>(base + o_oh);
+        ws.otc_bar = reinterpret_cast<unsigned*>(base + o_ob);
+        if (m > 0) {
+            ws.qr = reinterpret_cast<float*>(base + o_qr);
+            ws.ldr = ldr;
+            transpose_in<float>(ex, Qb, BKS_F32, m, len, ldq, ws.qr, ldr);   // qr[l][r] = Qb[r][l]
+        }
     }
     if (dtype == BKS_F64)
         orth_block<double>(ex, len, ldw, static_cast<const double*>(Qb), m, static_cast<double*>(W), c,
