@@ -302,7 +302,8 @@ struct Plan {
     CsrLayout csr;
     size_t td, td_bytes;     // scratch of the tridiagonal eigen-solve (0 bytes when it cannot run)
     size_t Qt, Bt, QBt, Pit, W, Wtmp, Wb, Wbtmp, part, og, rfac, ct, Rm, JX, lam, nrm, Vt,
-        order, Vk, stat, fpart, fgram, fbar, otc_part, otc_cts, otc_h, otc_bar, qr;
+        order, Vk, stat, fpart, fgram, fbar, otc_part, otc_cts, otc_h, otc_bar, qr, vtp, zt;
+    int64_t ldvt;         // row pitch of the padded copy of the Ritz coefficients (vtp)
     int64_t fcap, otc_cap, otc_ldct, ldr;
     int ldp;
     int64_t ldc;
@@ -372,6 +373,11 @@ Plan make_plan(const bks_matrix* A, int k, int q_eff, int w, size_t tb, int sms,
     p.Vt = a.take(size_t(w) * w * tb);
     p.order = a.take(size_t(w) * sizeof(int));
     p.Vk = a.take(size_t(kout) * p.ldd * tb);
+    // FP32: Z = Q Ubar_k and B Ubar_k on the tensor cores, from a copy of the coefficients
+    // with a 128-byte row pitch, through Z^T (kout x ldn)
+    p.ldvt = round_up(w, 32);
+    p.vtp = a.take(tb == 4 ? size_t(kout) * p.ldvt * 4 : 0);
+    p.zt = a.take(tb == 4 ? size_t(kout) * p.ldn * 4 : 0);
     {
         const bool fits = tb == 4 ? tridiag_fits<float>(w, kout) : tridiag_fits<double>(w, kout);
         p.td_bytes = fits ? tridiag_scratch_elems(w, kout) * tb : 0;
@@ -387,6 +393,10 @@ Plan make_plan(const bks_matrix* A, int k, int q_eff, int w, size_t tb, int sms,
     if (tb == 4) {
         const int64_t b = tc_partial_floats(w, d, w, sms);   // M = B^T B on the tensor cores
         if (b > p.tpart_cap) p.tpart_cap = b;
+        for (int64_t len : {n, d}) {                         // Q Ubar_k and B Ubar_k
+            const int64_t z = tc_partial_floats(w, len, kout, sms);
+            if (z > p.tpart_cap) p.tpart_cap = z;
+        }
     }
     if (on.tcap > p.tpart_cap) p.tpart_cap = on.tcap;
     if (od.tcap > p.tpart_cap) p.tpart_cap = od.tcap;
@@ -761,21 +771,49 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
         eig_path = use_td && tridiag_fits<T>(wr, kz) && topk_tridiag<T>(ex, wr, Rm, kz, Vt, wr, reinterpret_cast<T*>(base + p.td), ows) ? 1 : 0;
         if (eig_path == 0)
             sym_eig<T>(ex, wr, Rm, wr, JX, wr, lam, nrm, Vt, wr, order, sweeps, o.jacobi_tol, stat + 1);
-        // a7: Z = Q Ubar_k (row-major n x k)
-        GemmDesc gz{};
-        gz.M = kout; gz.N = n; gz.K = wr;
-        gz.X = Vt; gz.ldx = wr; gz.Y = Qt; gz.ldy = p.ldn;
-        gz.y_kmajor = false; gz.y_dtype = gm.y_dtype;
-        gz.out = Z; gz.ldo = kout; gz.out_transposed = true; gz.alpha = 1.0; gz.beta = 0.0;
-        gemm_simt<T>(ex, gz, part, p.part_cap);
+        // a7: Z = Q Ubar_k (row-major n x k).  FP32: on the tensor cores as
+        // Z^T = (Q_array^T X)^T with X = Ubar_k^T (rows of Vt, copied to a 128-byte pitch),
+        // then transposed; otherwise the CUDA-core kernel writes Z directly
+        KernelLog* klog_rr = ex.klog;   // the kernel log times products with A only
+        ex.klog = nullptr;
+        bool tc_ritz = false;
+        if (sizeof(T) == 4 && o.product_path != 1) {
+            float* vtp = reinterpret_cast<float*>(base + p.vtp);
+            float* zt = reinterpret_cast<float*>(base + p.zt);
+            cudaMemcpy2DAsync(vtp, size_t(p.ldvt) * 4, Vt, size_t(wr) * 4, size_t(wr) * 4, size_t(kout),
+                              cudaMemcpyDeviceToDevice, ex.stream);
+            tc_ritz = tc_product_f32(ex, reinterpret_cast<const float*>(Qt), wr, n, p.ldn, true, kout, vtp, p.ldvt,
+                                     zt, p.ldn, pw.xh, pw.xl, pw.tpart, pw.tpart_cap);
+            if (tc_ritz) transpose_in<T>(ex, zt, BKS_F32, kout, n, p.ldn, Z, kout);
+        }
+        if (!tc_ritz) {
+            GemmDesc gz{};
+            gz.M = kout; gz.N = n; gz.K = wr;
+            gz.X = Vt; gz.ldx = wr; gz.Y = Qt; gz.ldy = p.ldn;
+            gz.y_kmajor = false; gz.y_dtype = gm.y_dtype;
+            gz.out = Z; gz.ldo = kout; gz.out_transposed = true; gz.alpha = 1.0; gz.beta = 0.0;
+            gemm_simt<T>(ex, gz, part, p.part_cap);
+        }
         if (o.sign_fix) sign_fix<T>(ex, Z, n, kout, kout, Vt, wr, wr);
-        // sigma_i = |B ubar_i| = |A^T z_i|; V_k = B Ubar_k Sigma^{-1}
-        GemmDesc gv{};
-        gv.M = kout; gv.N = d; gv.K = wr;
-        gv.X = Vt; gv.ldx = wr; gv.Y = Bt; gv.ldy = p.ldd;
-        gv.y_kmajor = false; gv.y_dtype = gm.y_dtype;
-        gv.out = Vk; gv.ldo = p.ldd; gv.alpha = 1.0; gv.beta = 0.0;
-        gemm_simt<T>(ex, gv, part, p.part_cap);
+        // sigma_i = |B ubar_i| = |A^T z_i|; V_k = B Ubar_k Sigma^{-1} (same two routes, after
+        // the sign fix has flipped the rows of Vt)
+        bool tc_v = false;
+        if (tc_ritz) {
+            float* vtp = reinterpret_cast<float*>(base + p.vtp);
+            cudaMemcpy2DAsync(vtp, size_t(p.ldvt) * 4, Vt, size_t(wr) * 4, size_t(wr) * 4, size_t(kout),
+                              cudaMemcpyDeviceToDevice, ex.stream);
+            tc_v = tc_product_f32(ex, reinterpret_cast<const float*>(Bt), wr, d, p.ldd, true, kout, vtp, p.ldvt,
+                                  reinterpret_cast<float*>(Vk), p.ldd, pw.xh, pw.xl, pw.tpart, pw.tpart_cap);
+        }
+        if (!tc_v) {
+            GemmDesc gv{};
+            gv.M = kout; gv.N = d; gv.K = wr;
+            gv.X = Vt; gv.ldx = wr; gv.Y = Bt; gv.ldy = p.ldd;
+            gv.y_kmajor = false; gv.y_dtype = gm.y_dtype;
+            gv.out = Vk; gv.ldo = p.ldd; gv.alpha = 1.0; gv.beta = 0.0;
+            gemm_simt<T>(ex, gv, part, p.part_cap);
+        }
+        ex.klog = klog_rr;
         row_norms<T>(ex, Vk, kout, d, p.ldd, sigma, V != nullptr);
         if (V != nullptr)
             transpose_in<T>(ex, Vk, sizeof(T) == 8 ? BKS_F64 : BKS_F32, kout, d, p.ldd, V, kout);
