@@ -46,6 +46,8 @@ constexpr int OPT = 4;             // converted A stages in TMEM (TS form)
 constexpr int ACOL = 256;          // first TMEM column of the A stages (TS form)
 constexpr int RA_MAX = RAT > RA ? RAT : RA;
 constexpr int OP_MAX = OPT > OP ? OPT : OP;
+static_assert(x_ring(32) == OPT && x_ring(64) == OPT && x_ring(96) == OP && x_ring(128) == OP,
+              "the X ring and the converted-A ring share their release barriers");
 constexpr int NWARP = 11;
 constexpr int NTHREADS = NWARP * 32;
 constexpr uint32_t TILE_BYTES = BM * KC * 4;   // 16 KB
@@ -79,7 +81,7 @@ __device__ __forceinline__ float tf32_hi(float v) {
 struct Smem {
     uint64_t raw_full[RA_MAX], raw_empty[RA_MAX];
     uint64_t op_empty[OP_MAX], conv_full[OP_MAX];
-    uint64_t x_full[XR_MAX], x_empty[XR_MAX];
+    uint64_t x_full[XR_MAX];
     uint64_t acc_full[2], acc_empty[2];
     uint64_t drain;
     uint32_t tmem_base;
@@ -120,10 +122,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_init(&sm->op_empty[i], 1);
             mbar_init(&sm->conv_full[i], 4);
         }
-        for (int i = 0; i < XR; ++i) {
-            mbar_init(&sm->x_full[i], 1);
-            mbar_init(&sm->x_empty[i], 1);
-        }
+        for (int i = 0; i < XR; ++i) mbar_init(&sm->x_full[i], 1);
         for (int i = 0; i < 2; ++i) { mbar_init(&sm->acc_full[i], 1); mbar_init(&sm->acc_empty[i], 4); }
         mbar_init(&sm->drain, 1);
         sm->abort_flag = 0;
@@ -169,7 +168,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             UnitWalk w(ustart, p.cpt);
             int o = 0, ph = 0;
             for (int64_t u = ustart; u < uend; ++u, w.next()) {
-                if (!wait_bar(&sm->x_empty[o], uint32_t(ph ^ 1), abort_flag, p.status)) break;
+                // X stage o and converted-A stage o are released together by one commit
+                // (both rings are XR = NOP deep and advance with the unit index)
+                if (!wait_bar(&sm->op_empty[o], uint32_t(ph ^ 1), abort_flag, p.status)) break;
                 mbar_expect_tx(&sm->x_full[o], b_bytes);
                 unsigned char* dst = bop + o * b_bytes;
                 tma_load_2d(dst, &tmXh, w.kc * KC, 0, &sm->x_full[o]);
@@ -221,8 +222,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                 }
                 first = false;
-                umma_commit(&sm->op_empty[o]);
-                umma_commit(&sm->x_empty[xs]);
+                umma_commit(&sm->op_empty[o]);   // frees converted-A stage o and X stage xs (= o)
                 w.next();
                 if (u + 1 == uend || w.kc % FLUSH == 0)   // the next unit opens a window
                     umma_commit(&sm->acc_full[sub & 1]);
@@ -236,14 +236,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int ct = tid - 96;   // 0..127
         int i = 0;
         if constexpr (TS) {
-            // thread = TMEM lane = row m of the A tile (a warp reaches lanes 32 (warp % 4) ..)
+            // thread = TMEM lane = row m of the A tile (a warp reaches lanes 32 (warp % 4) ..).
+            // Software-pipelined over tiles with two register buffers: the next tile is read
+            // from shared memory while the current tile's stores to tensor memory are in
+            // flight (a tcgen05.st's source registers are free only after tcgen05.wait::st).
             const int m = (warp & 3) * 32 + lane;
             const uint32_t lane_addr = uint32_t((warp & 3) * 32) << 16;
-            for (int64_t u = ustart; u < uend; ++u, ++i) {
-                const int s = i % NRA, o = i % NOP;
-                if (!wait_bar(&sm->raw_full[s], uint32_t((i / NRA) & 1), abort_flag, p.status)) break;
+            // raw tile of unit i (stage i % NRA) -> hi / lo registers; releases the stage
+            auto load = [&](int ii, uint32_t (&h)[32], uint32_t (&l)[32]) -> bool {
+                const int s = ii % NRA;
+                if (!wait_bar(&sm->raw_full[s], uint32_t((ii / NRA) & 1), abort_flag, p.status)) return false;
                 const unsigned char* rs = raw + s * TILE_BYTES;
-                uint32_t h[32], l[32];
                 if (p.mode == 0) {   // 128B-swizzled K-major raw tile: row m's eight 16-byte chunks
                     const int rowoff = (m >> 3) * 1024 + (m & 7) * 128;
 #pragma unroll
@@ -269,16 +272,37 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sm->raw_empty[s]);   // the raw tile is in registers
-                if (!wait_bar(&sm->op_empty[o], uint32_t(((i / NOP) & 1) ^ 1), abort_flag, p.status)) break;
+                return true;
+            };
+            // registers of unit i -> converted-A stage i % NOP (after the stage is free)
+            auto store = [&](int ii, const uint32_t (&h)[32], const uint32_t (&l)[32]) -> bool {
+                const int o = ii % NOP;
+                if (!wait_bar(&sm->op_empty[o], uint32_t(((ii / NOP) & 1) ^ 1), abort_flag, p.status)) return false;
                 tc_fence_after();
                 const uint32_t col = tmem + lane_addr + uint32_t(ACOL + o * 64);
                 tmem_st32(col, h);
                 tmem_st32(col + 32, l);
+                return true;
+            };
+            auto publish = [&](int ii) {   // the stores of unit i have landed
                 tmem_wait_st();
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&sm->conv_full[o]);
+                if (lane == 0) mbar_arrive(&sm->conv_full[ii % NOP]);
+            };
+            const int nunits = int(uend - ustart);
+            uint32_t h0[32], l0[32], h1[32], l1[32];
+            bool ok = nunits > 0 && load(0, h0, l0);
+            for (int ii = 0; ok && ii < nunits; ii += 2) {
+                if (!store(ii, h0, l0)) break;
+                if (ii + 1 < nunits && !load(ii + 1, h1, l1)) { tmem_wait_st(); break; }
+                publish(ii);
+                if (ii + 1 >= nunits) break;
+                if (!store(ii + 1, h1, l1)) break;
+                if (ii + 2 < nunits && !load(ii + 2, h0, l0)) { tmem_wait_st(); break; }
+                publish(ii + 1);
             }
+            tmem_wait_st();
         } else
         for (int64_t u = ustart; u < uend; ++u, ++i) {
             const int s = i % RA, o = i % OP;
