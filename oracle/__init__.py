@@ -17,9 +17,12 @@ Modules
            GPU library also implements (from the published definitions).
   grad     exact adjoint of Sigma_k and A_k through a full SVD, plus central
            finite differences.
+  lanczos  Block Lanczos (Sec. 4): the three-term block recurrence with a block-
+           tridiagonal Q^T A A^T Q, with full, local or no reorthogonalisation.
 
-Every function here is pinned by ``tests/test_oracle_pins.py`` against closed
-forms, LAPACK, planted spectra, invariants and the worked example of Sec. 2.2.
+Every function here is pinned by ``tests/test_oracle_pins.py`` (and the Block Lanczos
+module by ``tests/test_oracle_lanczos.py``) against closed forms, LAPACK, planted
+spectra, invariants and the worked example of Sec. 2.2.
 """
-from . import krylov, jacobi, metrics, rng, grad  # noqa: F401
+from . import krylov, jacobi, metrics, rng, grad, lanczos  # noqa: F401
 from .krylov import block_krylov, simul_iter, dense_op, centred_csr_op  # noqa: F401
