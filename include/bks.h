@@ -141,7 +141,8 @@ bks_status bks_set_stream(bks_ctx* ctx, void* stream);
  * Later calls use it and allocate nothing while it is large enough; NULL reverts to
  * library-owned workspace.  Size it with bks_workspace_size. */
 bks_status bks_set_workspace(bks_ctx* ctx, void* ptr, size_t bytes);
-/* Workspace bytes a solve of A at rank k, q iterations needs. method: 0 BKI, 1 SI. */
+/* Workspace bytes a solve of A at rank k, q iterations needs. method: 0 BKI (and Block
+ * Lanczos), 1 SI. */
 bks_status bks_workspace_size(const bks_matrix* A, int k, int q, int method,
                               const bks_opts* opts, size_t* bytes);
 /* Fill *opts with the defaults described in bks_opts. */
@@ -193,6 +194,29 @@ bks_status bks_simul_iter(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint6
 bks_status bks_block_krylov_adaptive(bks_ctx* ctx, const bks_matrix* A, int k, int q_max, double tol,
                                      uint64_t seed, const void* pi, void* Z, void* sigma, void* V,
                                      const bks_opts* opts, bks_stats* stats);
+
+/* Block Lanczos (Sec. 4, "computing Q"): the classic method the paper relates Algorithm 2
+ * to.  Same Krylov space of A A^T from Q_0 = orth(A Pi), built by the three-term block
+ * recurrence
+ *   W_j = A A^T Q_j - Q_j D_j - Q_{j-1} R_{j-1}^T = Q_{j+1} R_j,   D_j = B_j^T B_j,
+ *   R_{j-1} = B_j^T B_{j-1},  B_j = A^T Q_j,
+ * so that the Rayleigh quotient T = Q^T A A^T Q is block tridiagonal (k x k blocks D_j on
+ * the diagonal, R_j below it, zero elsewhere).  Only that band is formed: no w x w product
+ * B^T B as in bks_block_krylov.  Rayleigh-Ritz then takes the k leading eigenvectors of T:
+ * Z = Q Ubar_k, sigma_i = |A^T z_i|, V as in bks_block_krylov.  The paper notes that the
+ * recurrence may need extra steps to stay numerically orthogonal; `reorth` chooses them:
+ *   BKS_REORTH_FULL   W_j is projected twice against every earlier block before its QR
+ *                     (Q is then the basis of bks_block_krylov, up to rounding);
+ *   BKS_REORTH_LOCAL  twice against Q_{j-1} and Q_j only (the blocks the recurrence uses);
+ *   BKS_REORTH_NONE   the recurrence alone (Q drifts from orthogonality once Ritz values
+ *                     converge; for study, not for results).
+ * The QR of W_j is CholeskyQR2 in every mode.  Other arguments, precisions, opts (except
+ * rr_mode, which does not apply) and errors as bks_block_krylov; q is capped the same
+ * way. */
+typedef enum { BKS_REORTH_FULL = 0, BKS_REORTH_LOCAL = 1, BKS_REORTH_NONE = 2 } bks_reorth;
+bks_status bks_block_lanczos(bks_ctx* ctx, const bks_matrix* A, int k, int q, int reorth, uint64_t seed,
+                             const void* pi, void* Z, void* sigma, void* V, const bks_opts* opts,
+                             bks_stats* stats);
 
 /* ---- building blocks (each one step of the path, exposed for tests and timing) ------ */
 

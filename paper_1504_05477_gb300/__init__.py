@@ -14,7 +14,7 @@ import ctypes
 from . import _binding as B
 from ._binding import BksError, BksMatrix, BksOpts, BksStats  # noqa: F401
 
-__all__ = ["block_krylov", "block_krylov_adaptive", "simul_iter", "matmul", "orthonormalize", "sym_eig", "gen_pi", "CsrMatrix",
+__all__ = ["block_krylov", "block_krylov_adaptive", "block_lanczos", "simul_iter", "matmul", "orthonormalize", "sym_eig", "gen_pi", "CsrMatrix",
            "ritz_triplets", "low_rank", "backward", "rand_svd", "krylov_width", "block_krylov_batched",
            "gen_pi_host", "Context", "context", "dense_matrix", "BksError", "lib_path"]
 
@@ -177,7 +177,7 @@ def _out_dtype(a, precision):
     return torch.float32
 
 
-def _solve(fn_name, a, k, q, seed, pi, want_v, precision, stats, _tol=None, **kw):
+def _solve(fn_name, a, k, q, seed, pi, want_v, precision, stats, _tol=None, _reorth=None, **kw):
     torch = _torch()
     mat, dev, odt = _as_bks(a, precision)
     ctx = context(dev)
@@ -195,6 +195,8 @@ def _solve(fn_name, a, k, q, seed, pi, want_v, precision, stats, _tol=None, **kw
     head = (ctx.ptr, ctypes.byref(mat), int(k), int(q))
     if _tol is not None:
         head = head + (ctypes.c_double(_tol),)
+    if _reorth is not None:
+        head = head + (int(_reorth),)
     status = fn(*head, ctypes.c_uint64(seed & (2**64 - 1)),
                 ctypes.c_void_p(pi.data_ptr()) if pi is not None else None,
                 ctypes.c_void_p(z.data_ptr()), ctypes.c_void_p(sig.data_ptr()),
@@ -219,6 +221,17 @@ def block_krylov_adaptive(a, k, q_max, tol, seed=0, pi=None, want_v=False, preci
     q_max iterations; stats["q_eff"] reports the iterations run."""
     return _solve("bks_block_krylov_adaptive", a, k, q_max, seed, pi, want_v, precision, stats,
                   _tol=float(tol), **kw)
+
+
+def block_lanczos(a, k, q, seed=0, pi=None, reorth="full", want_v=False, precision="auto", stats=False, **kw):
+    """Block Lanczos (Sec. 4; bks_block_lanczos): the Krylov space of Algorithm 2 built by
+    the three-term block recurrence, with Rayleigh-Ritz on the block-tridiagonal
+    T = Q^T A A^T Q.  reorth: "full" (twice against every earlier block), "local" (against
+    the two previous blocks) or "none".  Same interface and results as block_krylov."""
+    if reorth not in B.REORTH:
+        raise ValueError("reorth must be 'full', 'local' or 'none'")
+    return _solve("bks_block_lanczos", a, k, q, seed, pi, want_v, precision, stats,
+                  _reorth=B.REORTH[reorth], **kw)
 
 
 def simul_iter(a, k, q, seed=0, pi=None, want_v=False, precision="auto", stats=False, **kw):

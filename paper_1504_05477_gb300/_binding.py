@@ -15,6 +15,7 @@ BKS_ERR_TIMEOUT, BKS_ERR_UNSUPPORTED, BKS_WARN_DEFLATED = 7, 8, 100
 BKS_F64, BKS_F32, BKS_BF16 = 0, 1, 2
 BKS_DENSE, BKS_CSR = 0, 1
 PREC_AUTO, PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2, 3
+REORTH = {"full": 0, "local": 1, "none": 2}
 
 
 class BksMatrix(ctypes.Structure):
@@ -73,6 +74,8 @@ SIGNATURES = {
                                          _P, _P, _P, ctypes.POINTER(BksOpts), ctypes.POINTER(BksStats)]),
     "bks_simul_iter": (_I32, [_P, ctypes.POINTER(BksMatrix), _I32, _I32, _U64, _P, _P, _P, _P,
                               ctypes.POINTER(BksOpts), ctypes.POINTER(BksStats)]),
+    "bks_block_lanczos": (_I32, [_P, ctypes.POINTER(BksMatrix), _I32, _I32, _I32, _U64, _P, _P, _P, _P,
+                                 ctypes.POINTER(BksOpts), ctypes.POINTER(BksStats)]),
     "bks_gen_pi": (_I32, [_P, _U64, _I64, _I32, _I32, _P]),
     "bks_gen_pi_host": (_I32, [_U64, _I64, _I32, ctypes.POINTER(ctypes.c_float)]),
     "bks_csr_transpose": (_I32, [_P, ctypes.POINTER(BksMatrix), _P, _P, _P]),

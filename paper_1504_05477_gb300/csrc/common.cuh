@@ -244,4 +244,11 @@ void row_norms(Exec& ex, T* Vt, int k, int64_t len, int64_t ldv, T* sigma, bool 
 template <typename T>
 void check_finite(Exec& ex, const T* x, int64_t n);
 
+// Block Lanczos (Sec. 4): complete the block-tridiagonal T (w x w, row-major, ld w) whose
+// row blocks hold [R_{j-1} D_j] (k x k Gram products of the B blocks, lower band and
+// diagonal): the diagonal blocks are symmetrised, R_{j-1}^T is mirrored above the
+// diagonal and every block off the band is set to zero.
+template <typename T>
+void lanczos_band(Exec& ex, T* t, int w, int k);
+
 }  // namespace bks

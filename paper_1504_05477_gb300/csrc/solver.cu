@@ -302,8 +302,9 @@ struct Plan {
     CsrLayout csr;
     size_t td, td_bytes;     // scratch of the tridiagonal eigen-solve (0 bytes when it cannot run)
     size_t Qt, Bt, QBt, Pit, W, Wtmp, Wb, Wbtmp, part, og, rfac, ct, Rm, JX, lam, nrm, Vt,
-        order, Vk, stat, fpart, fgram, fbar, otc_part, otc_cts, otc_h, otc_bar, qr, vtp, zt;
+        order, Vk, stat, fpart, fgram, fbar, otc_part, otc_cts, otc_h, otc_bar, qr, vtp, zt, cf;
     int64_t ldvt;         // row pitch of the padded copy of the Ritz coefficients (vtp)
+    int64_t ldcf;         // row pitch of the Block Lanczos coefficients C_j (k x 2k)
     int64_t fcap, otc_cap, otc_ldct, ldr;
     int ldp;
     int64_t ldc;
@@ -322,6 +323,8 @@ int64_t max_partials(int64_t n, int64_t d, int k, int w, int sms) {
     upd(k, n, w);        // Z = Q Ubar_k
     upd(k, d, w);        // B Ubar_k
     upd(w, w, d);        // R = Q_B^T B
+    upd(k, 2 * k, d);    // Block Lanczos: [B_{j-1}; B_j]^T B_j
+    upd(k, n, 2 * k);    // Block Lanczos: W -= [Q_{j-1} Q_j] C_j
     return p;
 }
 
@@ -373,6 +376,8 @@ Plan make_plan(const bks_matrix* A, int k, int q_eff, int w, size_t tb, int sms,
     p.Vt = a.take(size_t(w) * w * tb);
     p.order = a.take(size_t(w) * sizeof(int));
     p.Vk = a.take(size_t(kout) * p.ldd * tb);
+    p.ldcf = round_up(2 * k, 32);
+    p.cf = a.take(size_t(k) * p.ldcf * tb);
     // FP32: Z = Q Ubar_k and B Ubar_k on the tensor cores, from a copy of the coefficients
     // with a 128-byte row pitch, through Z^T (kout x ldn)
     p.ldvt = round_up(w, 32);
@@ -396,6 +401,9 @@ Plan make_plan(const bks_matrix* A, int k, int q_eff, int w, size_t tb, int sms,
         for (int64_t len : {n, d}) {                         // Q Ubar_k and B Ubar_k
             const int64_t z = tc_partial_floats(w, len, kout, sms);
             if (z > p.tpart_cap) p.tpart_cap = z;
+            // Block Lanczos: the Gram [B_{j-1}; B_j]^T B_j and the update [Q_{j-1} Q_j] C_j
+            const int64_t l = tc_partial_floats(2 * k, len, k, sms);
+            if (l > p.tpart_cap) p.tpart_cap = l;
         }
     }
     if (on.tcap > p.tpart_cap) p.tpart_cap = on.tcap;
@@ -492,7 +500,7 @@ bks_status finish_solve(bks_ctx* ctx, bks_stats* st) {
 template <typename T>
 bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed, const void* pi,
                  void* Zv, void* sigv, void* Vv, const bks_opts& o, bks_stats* st, bool krylov,
-                 bool triplets, bool defer, double adapt_tol) {
+                 bool triplets, bool defer, double adapt_tol, int lanczos) {
     const int64_t n = A->n, d = A->d;
     // block size: the p >= kz columns of Pi (Sec. 8, spectral decay); kz Ritz vectors returned
     const int k = o.block_p > 0 ? o.block_p : kz;
@@ -557,9 +565,12 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
     // Eigen-solve: only Ubar_k is needed, so by default M = B^T B goes through the
     // tridiagonal top-k solver; the one-sided Jacobi covers Ritz triplets (all w vectors),
     // SI (w = k), widths beyond the tridiagonal kernels and eig_mode 1.
-    const bool use_td = !o.basis_only && !triplets && o.eig_mode != 1 && o.rr_mode != 1 && kz < w &&
+    // Block Lanczos (lanczos >= 0, the reorthogonalisation mode) forms T = Q^T A A^T Q from
+    // its block-tridiagonal band during the iteration; rr_mode does not apply to it.
+    const bool lz = krylov && lanczos >= 0;
+    const bool use_td = !o.basis_only && !triplets && o.eig_mode != 1 && (lz || o.rr_mode != 1) && kz < w &&
                         tridiag_fits<T>(w, kz);
-    const bool rr_qr = !use_td && (o.rr_mode == 1 || (o.rr_mode == 0 && w > 512));
+    const bool rr_qr = !lz && !use_td && (o.rr_mode == 1 || (o.rr_mode == 0 && w > 512));
     const bool bf16_mode = o.precision == BKS_PREC_BF16;
     const bool refine = bf16_mode && o.refine != 0;
     pw.bf16_pieces = bf16_mode ? 1 : 3;
@@ -615,18 +626,23 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
     }
     // Krylov blocks on the tensor-core kernel keep a row-major copy of Q (columns appended
     // block by block); once a block falls back to the CUDA-core kernel the copy is
-    // incomplete and the later blocks stay on the CUDA cores
-    bool qr_ok = krylov && p.otc_cap > 0;
+    // incomplete and the later blocks stay on the CUDA cores.  Block Lanczos with local
+    // reorthogonalisation reads a window of the copy starting at column (j-1)k, which the
+    // TMA takes only at a 16-byte aligned address (k a multiple of 4); without
+    // reorthogonalisation the copy is not read at all.
+    bool qr_ok = krylov && p.otc_cap > 0 &&
+                 (!lz || lanczos == BKS_REORTH_FULL || (lanczos == BKS_REORTH_LOCAL && k % 4 == 0));
     bool tc_ran = false;
-    auto orth = [&](int m, T* Qout) {
+    // W against the m orthonormal columns from Qb (column qcol of Q), result in Qout
+    auto orth = [&](int m, const T* Qb, int64_t qcol, T* Qout) {
         const int b = prof.begin();
         if (qr_ok) {
-            ows.qr = reinterpret_cast<float*>(base + p.qr);
+            ows.qr = reinterpret_cast<float*>(base + p.qr) + qcol;
             ows.ldr = p.ldr;
             ows.qr_append = true;
             ows.tc_used = &tc_ran;
         }
-        orth_block<T>(ex, n, p.ldn, Qt, m, W, k, Wtmp, Qout, ows);
+        orth_block<T>(ex, n, p.ldn, Qb, m, W, k, Wtmp, Qout, ows);
         if (qr_ok && !tc_ran) qr_ok = false;
         ows.qr = nullptr;
         ows.ldr = 0;
@@ -643,12 +659,63 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
         prof.end(1, b);
     };
 
+    // Block Lanczos, row block j of T: C_j = [B_{j-1}; B_j]^T B_j = [R_{j-1}^T; D_j] (B_0^T B_0
+    // alone at j = 0) into cf (k x ldcf, row i = column i of C_j), copied into rows jk..(j+1)k,
+    // columns (j-1)k..(j+1)k of T.  Returns the rows of C_j.
+    T* cf = reinterpret_cast<T*>(base + p.cf);
+    auto lz_coef = [&](int j) {
+        const int j0 = j > 0 ? j - 1 : 0;
+        const int rows = (j - j0 + 1) * k;
+        const T* Bw = Bt + size_t(j0) * k * p.ldd;
+        const T* Bj = Bt + size_t(j) * k * p.ldd;
+        KernelLog* klog = ex.klog;   // the kernel log times products with A only
+        ex.klog = nullptr;
+        const bool tc = sizeof(T) == 4 && o.product_path != 1 &&
+                        tc_product_f32(ex, reinterpret_cast<const float*>(Bw), rows, d, p.ldd, false, k,
+                                       reinterpret_cast<const float*>(Bj), p.ldd, reinterpret_cast<float*>(cf),
+                                       p.ldcf, pw.xh, pw.xl, pw.tpart, pw.tpart_cap);
+        ex.klog = klog;
+        if (!tc) {
+            GemmDesc g{};
+            g.M = k; g.N = rows; g.K = d;
+            g.X = Bj; g.ldx = p.ldd; g.Y = Bw; g.ldy = p.ldd;
+            g.y_kmajor = true; g.y_dtype = sizeof(T) == 8 ? BKS_F64 : BKS_F32;
+            g.out = cf; g.ldo = p.ldcf; g.alpha = 1.0; g.beta = 0.0;
+            gemm_simt<T>(ex, g, part, p.part_cap);
+        }
+        cudaMemcpy2DAsync(Rm + size_t(j) * k * w + size_t(j0) * k, size_t(w) * sizeof(T), cf,
+                          size_t(p.ldcf) * sizeof(T), size_t(rows) * sizeof(T), size_t(k),
+                          cudaMemcpyDeviceToDevice, ex.stream);
+    };
+    // The three-term recurrence: W = A A^T Q_j - Q_j D_j - Q_{j-1} R_{j-1}^T, i.e.
+    // W -= [Q_{j-1} Q_j] C_j with the C_j of lz_coef(j).
+    auto lz_sub = [&](int j) {
+        const int j0 = j > 0 ? j - 1 : 0;
+        const int rows = (j - j0 + 1) * k;
+        const T* Qw = Qt + size_t(j0) * k * p.ldn;
+        KernelLog* klog = ex.klog;
+        ex.klog = nullptr;
+        const bool tc = sizeof(T) == 4 && o.product_path != 1 &&
+                        tc_product_f32(ex, reinterpret_cast<const float*>(Qw), rows, n, p.ldn, true, k,
+                                       reinterpret_cast<const float*>(cf), p.ldcf, reinterpret_cast<float*>(W),
+                                       p.ldn, pw.xh, pw.xl, pw.tpart, pw.tpart_cap, true);
+        ex.klog = klog;
+        if (!tc) {
+            GemmDesc g{};
+            g.M = k; g.N = n; g.K = rows;
+            g.X = cf; g.ldx = p.ldcf; g.Y = Qw; g.ldy = p.ldn;
+            g.y_kmajor = false; g.y_dtype = sizeof(T) == 8 ? BKS_F64 : BKS_F32;
+            g.out = W; g.ldo = p.ldn; g.alpha = -1.0; g.beta = 1.0;
+            gemm_simt<T>(ex, g, part, p.part_cap);
+        }
+    };
+
     // Adaptive q: after B_{i-1} = A^T Q_{i-1}, the kz leading Ritz values of the i-block space
     // (M_i = B^T B over those blocks, tridiagonal form and multisection only); the
     // iteration stops at the first i >= 2 where none moved by more than adapt_tol
     // (relative) since i - 1 blocks.  B_{i-1} is then the last kept block: no product is
     // spent on the test.
-    const bool adaptive = krylov && adapt_tol > 0 && !o.basis_only && p.td_bytes > 0;
+    const bool adaptive = krylov && !lz && adapt_tol > 0 && !o.basis_only && p.td_bytes > 0;
     std::vector<double> prev_vals;
     auto stagnated = [&](int nb) -> bool {
         const int wc = nb * k;
@@ -701,7 +768,7 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
 
     // a1 + a4: W_0 = A Pi, Q_0 = orth(W_0)
     prod(false, Pit, p.ldd, W, p.ldn, k);
-    orth(0, Qt);
+    orth(0, Qt, 0, Qt);
     int q_run = q_eff;   // iterations run (fewer when the adaptive test stops early)
     bool stopped = false;
     for (int i = 1; i <= q_eff; ++i) {
@@ -715,10 +782,25 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
         }
         if (krylov && !o.basis_only && !refine && rr_qr) orth_b((i - 1) * k, Bprev);
         prod(false, Bprev, p.ldd, W, p.ldn, k);           // a3: W_i = A B_{i-1}
-        if (krylov)
-            orth(i * k, Qt + size_t(i) * k * p.ldn);     // a4: project + CholeskyQR2
-        else
-            orth(0, Qt);                                  // a9: SI re-orthonormalisation
+        if (lz) {
+            // Block Lanczos: the three-term recurrence, then the reorthogonalisation against
+            // every earlier block (full), against Q_{i-2} and Q_{i-1} (local) or none, and
+            // CholeskyQR2 (W = Q_i R_{i-1})
+            lz_coef(i - 1);
+            lz_sub(i - 1);
+            int m0 = 0, m = 0;
+            if (lanczos == BKS_REORTH_FULL) {
+                m = i * k;
+            } else if (lanczos == BKS_REORTH_LOCAL) {
+                m0 = i >= 2 ? i - 2 : 0;
+                m = (i - m0) * k;
+            }
+            orth(m, Qt + size_t(m0) * k * p.ldn, int64_t(m0) * k, Qt + size_t(i) * k * p.ldn);
+        } else if (krylov) {
+            orth(i * k, Qt, 0, Qt + size_t(i) * k * p.ldn);   // a4: project + CholeskyQR2
+        } else {
+            orth(0, Qt, 0, Qt);                               // a9: SI re-orthonormalisation
+        }
     }
     const int wr = krylov ? k * (q_run + 1) : k;   // width of the space Rayleigh-Ritz works on
     T* Blast = krylov ? Bt + size_t(q_run) * k * p.ldd : Bt;
@@ -731,6 +813,13 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
         prod(true, Qt, p.ldn, Bt, p.ldd, wr);
         if (krylov && !o.basis_only && rr_qr)
             for (int i = 0; i < q_run; ++i) orth_b(i * k, Bt + size_t(i) * k * p.ldd);
+    }
+    if (lz && !o.basis_only) {
+        // the last row block of T (all of them again from the refined B), then the band
+        if (refine)
+            for (int j = 0; j < q_run; ++j) lz_coef(j);
+        lz_coef(q_run);
+        lanczos_band<T>(ex, Rm, wr, k);
     }
 
     const int t_rr = prof.begin();
@@ -750,21 +839,24 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
         // fewer sweeps than on M itself and without accumulating V (Drmac & Veselic's
         // preconditioned Jacobi SVD).  Only the order of the column norms is used.
         if (rr_qr) orth_b(krylov ? q_run * k : 0, Blast);
-        GemmDesc gm{};
-        gm.M = wr; gm.N = wr; gm.K = d;
-        gm.X = rr_qr ? QBt : Bt; gm.ldx = p.ldd; gm.Y = Bt; gm.ldy = p.ldd;
-        gm.y_kmajor = true; gm.y_dtype = sizeof(T) == 8 ? BKS_F64 : BKS_F32;
-        gm.out = Rm; gm.ldo = wr; gm.alpha = 1.0; gm.beta = 0.0;
-        // FP32: on the tensor cores (3xTF32): row j of Rm = row j of (A X)^T with A = B and
-        // X = B (M, symmetric) or X = Q_B (row j of R = Q_B^T B)
-        KernelLog* klog = ex.klog;   // the kernel log times products with A only
-        ex.klog = nullptr;
-        const bool tc_m = sizeof(T) == 4 && o.product_path != 1 &&
-                          tc_product_f32(ex, reinterpret_cast<const float*>(Bt), wr, d, p.ldd, false, wr,
-                                         reinterpret_cast<const float*>(rr_qr ? QBt : Bt), p.ldd,
-                                         reinterpret_cast<float*>(Rm), wr, pw.xh, pw.xl, pw.tpart, pw.tpart_cap);
-        ex.klog = klog;
-        if (!tc_m) gemm_simt<T>(ex, gm, part, p.part_cap);
+        const int y_dtype = sizeof(T) == 8 ? BKS_F64 : BKS_F32;
+        if (!lz) {
+            GemmDesc gm{};
+            gm.M = wr; gm.N = wr; gm.K = d;
+            gm.X = rr_qr ? QBt : Bt; gm.ldx = p.ldd; gm.Y = Bt; gm.ldy = p.ldd;
+            gm.y_kmajor = true; gm.y_dtype = sizeof(T) == 8 ? BKS_F64 : BKS_F32;
+            gm.out = Rm; gm.ldo = wr; gm.alpha = 1.0; gm.beta = 0.0;
+            // FP32: on the tensor cores (3xTF32): row j of Rm = row j of (A X)^T with A = B and
+            // X = B (M, symmetric) or X = Q_B (row j of R = Q_B^T B)
+            KernelLog* klog = ex.klog;   // the kernel log times products with A only
+            ex.klog = nullptr;
+            const bool tc_m = sizeof(T) == 4 && o.product_path != 1 &&
+                              tc_product_f32(ex, reinterpret_cast<const float*>(Bt), wr, d, p.ldd, false, wr,
+                                             reinterpret_cast<const float*>(rr_qr ? QBt : Bt), p.ldd,
+                                             reinterpret_cast<float*>(Rm), wr, pw.xh, pw.xl, pw.tpart, pw.tpart_cap);
+            ex.klog = klog;
+            if (!tc_m) gemm_simt<T>(ex, gm, part, p.part_cap);
+        }   // Block Lanczos: Rm holds T already
         check_finite<T>(ex, Rm, int64_t(wr) * wr);
         // a6: eigen-decomposition of M, descending (row j of Rm is column j of R^T)
         const int sweeps = o.jacobi_max_sweeps > 0 ? o.jacobi_max_sweeps : 40;
@@ -790,7 +882,7 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
             GemmDesc gz{};
             gz.M = kout; gz.N = n; gz.K = wr;
             gz.X = Vt; gz.ldx = wr; gz.Y = Qt; gz.ldy = p.ldn;
-            gz.y_kmajor = false; gz.y_dtype = gm.y_dtype;
+            gz.y_kmajor = false; gz.y_dtype = y_dtype;
             gz.out = Z; gz.ldo = kout; gz.out_transposed = true; gz.alpha = 1.0; gz.beta = 0.0;
             gemm_simt<T>(ex, gz, part, p.part_cap);
         }
@@ -809,7 +901,7 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
             GemmDesc gv{};
             gv.M = kout; gv.N = d; gv.K = wr;
             gv.X = Vt; gv.ldx = wr; gv.Y = Bt; gv.ldy = p.ldd;
-            gv.y_kmajor = false; gv.y_dtype = gm.y_dtype;
+            gv.y_kmajor = false; gv.y_dtype = y_dtype;
             gv.out = Vk; gv.ldo = p.ldd; gv.alpha = 1.0; gv.beta = 0.0;
             gemm_simt<T>(ex, gv, part, p.part_cap);
         }
@@ -872,7 +964,7 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
 bks_status solve_entry(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed,
                        const void* pi, void* Z, void* sigma, void* V, const bks_opts* opts,
                        bks_stats* st, bool krylov, bool triplets = false, bool defer = false,
-                       double adapt_tol = 0.0) {
+                       double adapt_tol = 0.0, int lanczos = -1) {
     if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
     bks_status s = check_matrix(ctx, A);
     if (s != BKS_OK) return s;
@@ -906,9 +998,11 @@ bks_status solve_entry(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t
     }
     if (defer) o.profile = 0;
     if (prec == BKS_PREC_F64)
-        return solve<double>(ctx, A, k, q, seed, pi, Z, sigma, V, o, st, krylov, triplets, defer, adapt_tol);
+        return solve<double>(ctx, A, k, q, seed, pi, Z, sigma, V, o, st, krylov, triplets, defer, adapt_tol,
+                             lanczos);
     // BF16 and F32 both run the FP32 pipeline (Krylov blocks, Z, sigma in FP32)
-    return solve<float>(ctx, A, k, q, seed, pi, Z, sigma, V, o, st, krylov, triplets, defer, adapt_tol);
+    return solve<float>(ctx, A, k, q, seed, pi, Z, sigma, V, o, st, krylov, triplets, defer, adapt_tol,
+                        lanczos);
 }
 
 }  // namespace
@@ -1099,6 +1193,15 @@ bks_status bks_simul_iter(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint6
                           const void* pi, void* Z, void* sigma, void* V, const bks_opts* opts,
                           bks_stats* stats) {
     return solve_entry(ctx, A, k, q, seed, pi, Z, sigma, V, opts, stats, false);
+}
+
+bks_status bks_block_lanczos(bks_ctx* ctx, const bks_matrix* A, int k, int q, int reorth, uint64_t seed,
+                             const void* pi, void* Z, void* sigma, void* V, const bks_opts* opts,
+                             bks_stats* stats) {
+    if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
+    if (reorth != BKS_REORTH_FULL && reorth != BKS_REORTH_LOCAL && reorth != BKS_REORTH_NONE)
+        return fail(ctx, BKS_ERR_INVALID_ARG, "reorth must be BKS_REORTH_FULL, _LOCAL or _NONE");
+    return solve_entry(ctx, A, k, q, seed, pi, Z, sigma, V, opts, stats, true, false, false, 0.0, reorth);
 }
 
 bks_status bks_block_krylov_batched(bks_ctx* ctx, int batch, const bks_matrix* As, int k, int q,
