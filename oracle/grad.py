@@ -34,27 +34,36 @@ def loss(a, k, t):
     return float(s[:k].sum() + np.sum((ak - t) ** 2))
 
 
-def adjoint(a, k, g_sigma, g_ak):
-    """dL/dA for upstream gradients g_sigma (k) and g_ak (n x d, or None)."""
-    a64 = np.asarray(a, dtype=np.float64)
-    u, s, v, _ = truncated(a64, k)
-    n, d = a64.shape
+def adjoint_from_triplets(u, s, v, k, g_sigma, g_ak, gap_tau=0.0):
+    """The formula above with the given triplets (u: n x r, s: r descending, v: d x r) in
+    place of a full SVD; (I - U U^T) then projects out the span of the given u.  It is the
+    exact gradient when the triplets span range(A) (e.g. A of rank <= r).  With gap_tau > 0,
+    c_ij is taken as 0 where lambda_i - lambda_j <= gap_tau lambda_1 (near-degenerate pairs)."""
+    u, s, v = (np.asarray(x, dtype=np.float64) for x in (u, s, v))
     g_sigma = np.asarray(g_sigma, dtype=np.float64)
-    out = (u[:, :k] * g_sigma) @ v[:, :k].T
+    uk, vk = u[:, :k], v[:, :k]
+    out = (uk * g_sigma) @ vk.T
     if g_ak is None:
         return out
     g = np.asarray(g_ak, dtype=np.float64)
-    uk, vk = u[:, :k], v[:, :k]
     out += uk @ (uk.T @ g)
     utgv = u.T @ g @ v                               # (r x r): entry (a, b) = u_a^T G v_b
     si = s[:k][:, None]
     sj = s[k:][None, :]
     lam_gap = si ** 2 - sj ** 2
-    c = (si * utgv[k:, :k].T + sj * utgv[:k, k:]) / lam_gap      # (k x r-k)
+    keep = lam_gap > gap_tau * s[0] ** 2
+    c = np.where(keep, (si * utgv[k:, :k].T + sj * utgv[:k, k:]) / np.where(keep, lam_gap, 1.0), 0.0)
     out += u[:, k:] @ (c.T * s[:k][None, :]) @ vk.T
     out += uk @ (c * s[k:][None, :]) @ v[:, k:].T
     out += (g @ vk - u @ (u.T @ (g @ vk))) @ vk.T
     return out
+
+
+def adjoint(a, k, g_sigma, g_ak):
+    """dL/dA for upstream gradients g_sigma (k) and g_ak (n x d, or None), through LAPACK's
+    full thin SVD of A."""
+    u, s, v, _ = truncated(a, k)
+    return adjoint_from_triplets(u, s, v, k, g_sigma, g_ak)
 
 
 def loss_grad(a, k, t):

@@ -409,3 +409,24 @@ def test_adaptive_changes_are_nonnegative_and_ritz_values_monotone():
         prev = s
     res, deltas = krylov.block_krylov_adaptive(a, 8, 6, 1e-6, pi)
     assert all(d >= 0 for d in deltas) and res.q_eff <= 6
+
+
+def test_adjoint_from_truncated_triplets_when_they_span_the_range():
+    """adjoint_from_triplets with only the leading r' of the triplets: exact (against central
+    differences) when A has rank <= r', i.e. when the given triplets span range(A) -- the
+    situation of a Krylov space that holds range(A).  With a triplet of the range left out
+    it is not (the pin bites)."""
+    rng = np.random.default_rng(41)
+    n, d, rank, k = 30, 24, 9, 4
+    u0 = np.linalg.qr(rng.standard_normal((n, rank)))[0]
+    v0 = np.linalg.qr(rng.standard_normal((d, rank)))[0]
+    a = (u0 * (1.0 / np.arange(1, rank + 1))) @ v0.T
+    t = rng.standard_normal((n, d))
+    u, s, v, ak = grad.truncated(a, k)
+    g_ak = 2.0 * (ak - t)
+    fd = grad.central_difference(a, k, t)
+    r = 12   # >= rank
+    got = grad.adjoint_from_triplets(u[:, :r], s[:r], v[:, :r], k, np.ones(k), g_ak)
+    assert np.linalg.norm(got - fd) / np.linalg.norm(fd) < 1e-6
+    short = grad.adjoint_from_triplets(u[:, :rank - 1], s[:rank - 1], v[:, :rank - 1], k, np.ones(k), g_ak)
+    assert np.linalg.norm(short - fd) / np.linalg.norm(fd) > 1e-3
