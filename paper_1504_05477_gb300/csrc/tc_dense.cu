@@ -354,10 +354,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // ---------------------------------------------------------------- epilogue
         const int grp = warp & 3;                 // TMEM lanes 32*grp .. 32*grp+31
         const int m = grp * 32 + lane;            // row of D owned by this thread
+        // A failed wait (timeout or abort) clears `ok`; the warp then keeps walking the same
+        // segments without touching TMEM or the output, so that the four warps always meet
+        // at the same named barriers.
         int seg = -1, sub = -1;
         int64_t u = ustart;
         bool ok = true;
-        while (u < uend && ok) {
+        while (u < uend) {
             const int64_t t = u / p.cpt;
             const int64_t seg_end = (t + 1) * p.cpt < uend ? (t + 1) * p.cpt : uend;
             const bool whole = (u == t * p.cpt) && (seg_end == (t + 1) * p.cpt);
@@ -374,9 +377,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 int64_t w_end = u + (FLUSH - kc % FLUSH);
                 if (w_end > seg_end) w_end = seg_end;
                 ++sub;
-                if (!wait_bar(&sm->acc_full[sub & 1], uint32_t((sub >> 1) & 1), abort_flag, p.status)) {
+                if (ok && !wait_bar(&sm->acc_full[sub & 1], uint32_t((sub >> 1) & 1), abort_flag, p.status))
                     ok = false;
-                    break;
+                if (!ok) {
+                    u = w_end;
+                    continue;
                 }
                 tc_fence_after();
                 const uint32_t acc = tmem + uint32_t(sub & 1) * ACC_STRIDE + (uint32_t(grp * 32) << 16);
@@ -408,7 +413,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 if (lane == 0) mbar_arrive(&sm->acc_empty[sub & 1]);
                 u = w_end;
             }
-            if (!ok) break;
             const int64_t row = t * BM + m;
             float* dst;
             int64_t stride;
@@ -420,7 +424,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 dst = p.part + slot * int64_t(CP) * BM + m;
                 stride = BM;
             }
-            if (whole && p.accumulate) {
+            if (!ok || *abort_flag) {
+                // nothing is written after a failed wait
+            } else if (whole && p.accumulate) {
                 if (row < p.rows_out) {
 #pragma unroll
                     for (int j = 0; j < CP; ++j)
@@ -441,9 +447,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int64_t cc = c_first; cc <= c_last; ++cc) ncontrib += ((cc + 1) * U) / G != (cc * U) / G;
                 __threadfence();
                 asm volatile("bar.sync 1, 128;" ::: "memory");   // the four epilogue warps
-                if (m == 0) fix_last = atomicAdd(&p.tile_cnt[t], 1u) == unsigned(ncontrib - 1);
+                if (m == 0) fix_last = ok && atomicAdd(&p.tile_cnt[t], 1u) == unsigned(ncontrib - 1);
                 asm volatile("bar.sync 1, 128;" ::: "memory");
-                if (fix_last) {
+                if (fix_last && !*abort_flag) {
                     __threadfence();
                     float v[CP];
 #pragma unroll
