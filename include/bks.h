@@ -297,6 +297,17 @@ bks_status bks_ritz_triplets(bks_ctx* ctx, const bks_matrix* A, int k, int q, ui
                              const void* pi, int method, void* U, void* sigma, void* V,
                              const bks_opts* opts, bks_stats* stats);
 
+/* The Ritz triplets of a batch of independent matrices (the forward state of a batched
+ * forward and backward): for each i, as bks_ritz_triplets on As[i], Us[i] (n_i x w_i),
+ * sigmas[i] (w_i) and Vs[i] (d_i x w_i), w_i = bks_krylov_width(n_i, d_i, k, q, method).
+ * Streams, host threads, seeds, pis, statuses and the return value as for
+ * bks_block_krylov_batched; every result is that of the single call.  Synchronises the
+ * streams. */
+bks_status bks_ritz_triplets_batched(bks_ctx* ctx, int batch, const bks_matrix* As, int k, int q,
+                                     const uint64_t* seeds, const void* const* pis, int method,
+                                     void* const* Us, void* const* sigmas, void* const* Vs,
+                                     const bks_opts* opts, bks_status* statuses);
+
 /* Gradient of a loss through Sigma_k and A_k = Z Z^T A with respect to A, from the w Ritz
  * triplets (U n x w, sigma w, V d x w, row-major, as written by bks_ritz_triplets).  No
  * counterpart in the paper, which does not differentiate its outputs.  g_sigma (k,
@@ -311,6 +322,18 @@ bks_status bks_ritz_triplets(bks_ctx* ctx, const bks_matrix* A, int k, int q, ui
 bks_status bks_backward(bks_ctx* ctx, int dtype, int64_t n, int64_t d, int k, int w,
                         const void* U, const void* sigma, const void* V, const void* g_sigma,
                         const void* G, void* dA, double gap_tau);
+
+/* bks_backward for a batch of independent solves: matrix i is ns[i] x ds[i] with Krylov
+ * width ws[i], triplets Us[i], sigmas[i], Vs[i] (as written by bks_ritz_triplets_batched),
+ * upstream gradients g_sigmas[i] (k) and Gs[i] (ns[i] x ds[i]) -- either array may be NULL,
+ * and so may its entries, but not both for one matrix -- and output dAs[i].  The calls run
+ * on the context's batch streams from several host threads; each result is that of
+ * bks_backward.  statuses (host, may be NULL) receives each status; the return value is
+ * the first error, else BKS_OK.  Synchronises the streams. */
+bks_status bks_backward_batched(bks_ctx* ctx, int dtype, int batch, const int64_t* ns, const int64_t* ds,
+                                int k, const int* ws, const void* const* Us, const void* const* sigmas,
+                                const void* const* Vs, const void* const* g_sigmas, const void* const* Gs,
+                                void* const* dAs, double gap_tau, bks_status* statuses);
 
 /* out (n x d row-major) = U_r diag(sigma_r) V_r^T with the first r columns of U (n x ldu)
  * and V (d x ldv), row-major, dtype BKS_F32 or BKS_F64: the rank-r approximation

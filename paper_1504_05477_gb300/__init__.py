@@ -16,6 +16,7 @@ from ._binding import BksError, BksMatrix, BksOpts, BksStats  # noqa: F401
 
 __all__ = ["block_krylov", "block_krylov_adaptive", "block_lanczos", "simul_iter", "matmul", "orthonormalize", "sym_eig", "gen_pi", "CsrMatrix",
            "ritz_triplets", "low_rank", "backward", "rand_svd", "krylov_width", "block_krylov_batched",
+           "ritz_triplets_batched", "backward_batched", "rand_svd_batched",
            "gen_pi_host", "Context", "context", "dense_matrix", "BksError", "lib_path"]
 
 
@@ -398,36 +399,181 @@ def _autograd_function():
     torch = _torch()
 
     class RandSVD(torch.autograd.Function):
-        """(Sigma_k, A_k = Z Z^T A) of a randomized solve, differentiable in A.  The Ritz
-        triplets are the saved forward state; the backward is one bks_backward call (not
-        an unrolling of the iterations)."""
+        """(Sigma_k, A_k = Z Z^T A) of a randomized solve, differentiable in A.  The backward
+        is one bks_backward call on the Ritz triplets (not an unrolling of the iterations).
+        The triplets are saved by the forward, or (recompute) rebuilt in the backward by the
+        same deterministic solve, which then holds only A and Pi."""
 
         @staticmethod
-        def forward(ctx, a, k, q, seed, pi, method, precision, gap_tau):
+        def forward(ctx, a, k, q, seed, pi, method, precision, gap_tau, recompute):
             u, s, v = ritz_triplets(a.detach(), k, q, seed=seed, pi=pi, method=method, precision=precision)
-            ctx.save_for_backward(u, s, v)
-            ctx.k, ctx.gap_tau, ctx.in_dtype = k, gap_tau, a.dtype
+            if recompute:
+                if pi is not None:
+                    ctx.save_for_backward(a, pi)
+                else:
+                    ctx.save_for_backward(a)
+            else:
+                ctx.save_for_backward(u, s, v)
+            ctx.k, ctx.q, ctx.seed, ctx.method, ctx.precision = k, q, seed, method, precision
+            ctx.gap_tau, ctx.in_dtype, ctx.recompute = gap_tau, a.dtype, recompute
             return s[:k].clone(), low_rank(u, s, v, k)
 
         @staticmethod
         def backward(ctx, g_sigma, g_ak):
-            u, s, v = ctx.saved_tensors
+            if ctx.recompute:
+                saved = ctx.saved_tensors
+                a, pi = saved[0], (saved[1] if len(saved) > 1 else None)
+                u, s, v = ritz_triplets(a.detach(), ctx.k, ctx.q, seed=ctx.seed, pi=pi, method=ctx.method,
+                                        precision=ctx.precision)
+            else:
+                u, s, v = ctx.saved_tensors
             da = backward(u, s, v, ctx.k, g_sigma, g_ak, ctx.gap_tau)
-            return da.to(ctx.in_dtype), None, None, None, None, None, None, None
+            return da.to(ctx.in_dtype), None, None, None, None, None, None, None, None
 
-    return RandSVD
+    class RandSVDBatched(torch.autograd.Function):
+        """rand_svd on a list of matrices: one batched triplets call forward, one batched
+        backward call (bks_ritz_triplets_batched, bks_backward_batched)."""
+
+        @staticmethod
+        def forward(ctx, k, q, seeds, pis, method, precision, gap_tau, recompute, *mats):
+            trips = ritz_triplets_batched([m.detach() for m in mats], k, q, seeds=seeds, pis=pis, method=method,
+                                          precision=precision)
+            ctx.k, ctx.q, ctx.seeds, ctx.pis, ctx.method = k, q, seeds, pis, method
+            ctx.precision, ctx.gap_tau, ctx.recompute = precision, gap_tau, recompute
+            ctx.in_dtypes = [m.dtype for m in mats]
+            if recompute:
+                ctx.save_for_backward(*mats)
+            else:
+                ctx.save_for_backward(*[x for t in trips for x in t])
+            out = []
+            for u, s, v in trips:
+                out += [s[:k].clone(), low_rank(u, s, v, k)]
+            return tuple(out)
+
+        @staticmethod
+        def backward(ctx, *grads):
+            saved = ctx.saved_tensors
+            if ctx.recompute:
+                trips = ritz_triplets_batched([m.detach() for m in saved], ctx.k, ctx.q, seeds=ctx.seeds,
+                                              pis=ctx.pis, method=ctx.method, precision=ctx.precision)
+            else:
+                trips = [tuple(saved[3 * i:3 * i + 3]) for i in range(len(saved) // 3)]
+            das = backward_batched(trips, ctx.k, list(grads[0::2]), list(grads[1::2]), ctx.gap_tau)
+            return (None,) * 8 + tuple(da.to(dt) for da, dt in zip(das, ctx.in_dtypes))
+
+    return RandSVD, RandSVDBatched
 
 
 _RANDSVD = None
 
 
-def rand_svd(a, k, q, seed=0, pi=None, method="bki", precision="auto", gap_tau=0.0):
+def rand_svd(a, k, q, seed=0, pi=None, method="bki", precision="auto", gap_tau=0.0, recompute=False):
     """Differentiable (Sigma_k, A_k) of Block Krylov (method "bki") or Simultaneous
-    Iteration ("si") on a dense CUDA matrix."""
+    Iteration ("si") on a dense CUDA matrix.  recompute=True keeps no Ritz triplets between
+    forward and backward (only A and Pi) and rebuilds them in the backward; the gradient is
+    bit-identical, since the solve is deterministic."""
     global _RANDSVD
     if _RANDSVD is None:
         _RANDSVD = _autograd_function()
-    return _RANDSVD.apply(a, k, q, seed, pi, method, precision, gap_tau)
+    return _RANDSVD[0].apply(a, k, q, seed, pi, method, precision, gap_tau, bool(recompute))
+
+
+def rand_svd_batched(mats, k, q, seeds=None, pis=None, method="bki", precision="auto", gap_tau=0.0,
+                     recompute=False):
+    """rand_svd on a list of dense CUDA matrices of any shapes, forward and backward each in
+    one batched call.  Returns [(Sigma_k, A_k), ...], differentiable in every matrix."""
+    global _RANDSVD
+    if _RANDSVD is None:
+        _RANDSVD = _autograd_function()
+    if len(mats) == 0:
+        return []
+    flat = _RANDSVD[1].apply(k, q, seeds, pis, method, precision, gap_tau, bool(recompute), *mats)
+    return [(flat[2 * i], flat[2 * i + 1]) for i in range(len(mats))]
+
+
+def ritz_triplets_batched(mats, k, q, seeds=None, pis=None, method="bki", precision="auto", **kw):
+    """ritz_triplets on a list of dense CUDA matrices (or CsrMatrix) in one call
+    (bks_ritz_triplets_batched): a list of (U_i, sigma_i, V_i)."""
+    torch = _torch()
+    b = len(mats)
+    if b == 0:
+        return []
+    arr = (BksMatrix * b)()
+    up, sp, vp, pp = ((ctypes.c_void_p * b)() for _ in range(4))
+    outs, dev = [], None
+    for i, a in enumerate(mats):
+        m, dv, odt = _as_bks(a, precision)
+        dev = dv if dev is None else dev
+        arr[i] = m
+        w = krylov_width(m.n, m.d, k, q, method)
+        if w < 1:
+            raise ValueError(f"bad sizes for matrix {i}")
+        u = torch.empty((m.n, w), dtype=odt, device=dv)
+        s = torch.empty((w,), dtype=odt, device=dv)
+        v = torch.empty((m.d, w), dtype=odt, device=dv)
+        up[i], sp[i], vp[i] = u.data_ptr(), s.data_ptr(), v.data_ptr()
+        if pis is not None and pis[i] is not None:
+            p = pis[i]
+            if p.shape != (m.d, k) or p.dtype != odt or not p.is_contiguous():
+                raise ValueError(f"pis[{i}] must be a contiguous {m.d}x{k} {odt} tensor")
+            pp[i] = p.data_ptr()
+        outs.append((u, s, v))
+    ctx = context(dev)
+    seeds_arr = (ctypes.c_uint64 * b)(*[int(x) & (2**64 - 1) for x in (seeds if seeds is not None else range(b))])
+    statuses = (ctypes.c_int32 * b)()
+    opts = _opts(precision=precision, **kw)
+    status = ctx.lib.bks_ritz_triplets_batched(ctx.ptr, b, arr, int(k), int(q), ctypes.cast(seeds_arr, ctypes.c_void_p),
+                                               ctypes.cast(pp, ctypes.c_void_p) if pis is not None else None,
+                                               0 if method == "bki" else 1, ctypes.cast(up, ctypes.c_void_p),
+                                               ctypes.cast(sp, ctypes.c_void_p), ctypes.cast(vp, ctypes.c_void_p),
+                                               ctypes.byref(opts), ctypes.cast(statuses, ctypes.c_void_p))
+    B.check(status, ctx.ptr, "bks_ritz_triplets_batched")
+    return outs
+
+
+def backward_batched(triplets, k, g_sigmas=None, g_aks=None, gap_tau=0.0):
+    """backward for a list of Ritz triplets (bks_backward_batched).  g_sigmas / g_aks: lists
+    (entries may be None) or None.  Returns the list of dL/dA_i."""
+    torch = _torch()
+    b = len(triplets)
+    if b == 0:
+        return []
+    dt = triplets[0][0].dtype
+    ns, ds_, ws = (ctypes.c_int64 * b)(), (ctypes.c_int64 * b)(), (ctypes.c_int32 * b)()
+    up, sp, vp, gp, Gp, dp = ((ctypes.c_void_p * b)() for _ in range(6))
+    keep, das = [], []
+    for i, (u, s, v) in enumerate(triplets):
+        u, s, v = u.contiguous(), s.contiguous(), v.contiguous()
+        if u.dtype != dt:
+            raise ValueError("every triplet must have the same dtype")
+        n, w = u.shape
+        d = v.shape[0]
+        ns[i], ds_[i], ws[i] = n, d, w
+        up[i], sp[i], vp[i] = u.data_ptr(), s.data_ptr(), v.data_ptr()
+        gs = g_sigmas[i] if g_sigmas is not None else None
+        ga = g_aks[i] if g_aks is not None else None
+        gs = gs.contiguous().to(dt) if gs is not None else None
+        ga = ga.contiguous().to(dt) if ga is not None else None
+        if gs is None and ga is None:
+            gs = torch.zeros((k,), dtype=dt, device=u.device)
+        if gs is not None:
+            gp[i] = gs.data_ptr()
+        if ga is not None:
+            Gp[i] = ga.data_ptr()
+        da = torch.empty((n, d), dtype=dt, device=u.device)
+        dp[i] = da.data_ptr()
+        keep += [u, s, v, gs, ga]
+        das.append(da)
+    ctx = context(triplets[0][0].device)
+    statuses = (ctypes.c_int32 * b)()
+    B.check(ctx.lib.bks_backward_batched(ctx.ptr, _dtype_code(dt), b, ctypes.cast(ns, ctypes.c_void_p),
+                                         ctypes.cast(ds_, ctypes.c_void_p), int(k), ctypes.cast(ws, ctypes.c_void_p),
+                                         ctypes.cast(up, ctypes.c_void_p), ctypes.cast(sp, ctypes.c_void_p),
+                                         ctypes.cast(vp, ctypes.c_void_p), ctypes.cast(gp, ctypes.c_void_p),
+                                         ctypes.cast(Gp, ctypes.c_void_p), ctypes.cast(dp, ctypes.c_void_p),
+                                         float(gap_tau), ctypes.cast(statuses, ctypes.c_void_p)),
+            ctx.ptr, "bks_backward_batched")
+    return das
 
 
 # ---------------------------------------------------------------------- batches

@@ -89,6 +89,10 @@ SIGNATURES = {
     "bks_ritz_triplets": (_I32, [_P, ctypes.POINTER(BksMatrix), _I32, _I32, _U64, _P, _I32, _P, _P, _P,
                                  ctypes.POINTER(BksOpts), ctypes.POINTER(BksStats)]),
     "bks_backward": (_I32, [_P, _I32, _I64, _I64, _I32, _I32, _P, _P, _P, _P, _P, _P, ctypes.c_double]),
+    "bks_ritz_triplets_batched": (_I32, [_P, _I32, ctypes.POINTER(BksMatrix), _I32, _I32, _P, _P, _I32, _P, _P,
+                                         _P, ctypes.POINTER(BksOpts), _P]),
+    "bks_backward_batched": (_I32, [_P, _I32, _I32, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P, ctypes.c_double,
+                                    _P]),
     "bks_low_rank": (_I32, [_P, _I32, _I64, _I64, _I32, _P, _I64, _P, _P, _I64, _P]),
 }
 

@@ -1005,6 +1005,135 @@ bks_status solve_entry(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t
                         lanczos);
 }
 
+
+// ------------------------------------------------------------------- batches
+// Up to S stream contexts of ctx (created on first use, each with its own stream).
+bks_status ensure_subs(bks_ctx* ctx, int S) {
+    while (int(ctx->subs.size()) < S) {
+        bks_ctx* sub = nullptr;
+        bks_status cs = bks_create(&sub, ctx->device);
+        if (cs != BKS_OK) return fail(ctx, cs, "could not create a stream context for the batch");
+        if (cudaStreamCreateWithFlags(&sub->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            bks_destroy(sub);
+            return fail(ctx, BKS_ERR_CUDA, "could not create a stream for the batch");
+        }
+        sub->own_stream = true;
+        ctx->subs.push_back(sub);
+    }
+    return BKS_OK;
+}
+
+// The batch starts after the work already queued on the caller's stream ...
+cudaEvent_t batch_begin(bks_ctx* ctx, int S) {
+    cudaEvent_t start;
+    cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
+    cudaEventRecord(start, ctx->stream);
+    for (int j = 0; j < S; ++j) cudaStreamWaitEvent(ctx->subs[j]->stream, start, 0);
+    return start;
+}
+
+// ... and later work on the caller's stream is ordered after the batch.
+void batch_end(bks_ctx* ctx, int S, cudaEvent_t ev) {
+    for (int j = 0; j < S; ++j) {
+        cudaEventRecord(ev, ctx->subs[j]->stream);
+        cudaStreamWaitEvent(ctx->stream, ev, 0);
+    }
+    cudaEventDestroy(ev);
+}
+
+// worker(0) .. worker(T - 1): worker 0, and any that could not be given a thread, run here.
+template <typename F>
+void run_workers(int T, F&& worker) {
+    tc::encode_fn();   // the tensor-map encoder's one-time lookup, before the threads start
+    std::vector<std::thread> threads;
+    int started = 0;   // threads 1 .. started run concurrently; the rest run here
+    try {
+        for (int t = 1; t < T; ++t, ++started) threads.emplace_back(worker, t);
+    } catch (...) {
+    }
+    worker(0);
+    for (int t = started + 1; t < T; ++t) worker(t);
+    for (std::thread& th : threads) th.join();
+}
+
+// Independent solves (Algorithm 2 or 1, or their Ritz triplets) on the stream contexts.
+bks_status batched_solve(bks_ctx* ctx, int batch, const bks_matrix* As, int k, int q, const uint64_t* seeds,
+                         const void* const* pis, void* const* Zs, void* const* sigmas, void* const* Vs,
+                         const bks_opts* opts, bks_stats* stats, bks_status* statuses, bool krylov, bool triplets,
+                         const char* what) {
+    if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
+    if (batch < 0 || (batch > 0 && (As == nullptr || Zs == nullptr || sigmas == nullptr)))
+        return fail(ctx, BKS_ERR_INVALID_ARG, std::string("bad ") + what + " arguments");
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (batch == 0) return BKS_OK;
+    DeviceGuard g(ctx->device);
+    const int S = batch < BKS_BATCH_STREAMS ? batch : BKS_BATCH_STREAMS;
+    bks_status cs = ensure_subs(ctx, S);
+    if (cs != BKS_OK) return cs;
+    {   // size every stream's workspace for the largest matrix once (no reallocation mid-batch)
+        size_t need = 0;
+        for (int i = 0; i < batch; ++i) {
+            size_t b = 0;
+            if (bks_workspace_size(&As[i], k, q, krylov ? 0 : 1, opts, &b) == BKS_OK && b > need) need = b;
+        }
+        for (int j = 0; j < S; ++j)
+            if (need > 0 && ensure_ws(ctx->subs[j], need) != BKS_OK)
+                return fail(ctx, BKS_ERR_NOMEM, "could not allocate the batch workspaces");
+    }
+    cudaEvent_t start = batch_begin(ctx, S);
+    bks_status worst = BKS_OK;
+    auto note = [&](int i, bks_status st_i, const bks_stats& one) {
+        if (statuses) statuses[i] = st_i;
+        if (st_i != BKS_OK && (worst == BKS_OK || (worst == BKS_WARN_DEFLATED && st_i != BKS_WARN_DEFLATED)))
+            worst = st_i;
+        if (stats) {
+            stats->q_eff = one.q_eff;
+            stats->width = one.width;
+            stats->jacobi_sweeps = one.jacobi_sweeps > stats->jacobi_sweeps ? one.jacobi_sweeps : stats->jacobi_sweeps;
+            stats->chol_shifts += one.chol_shifts;
+            stats->launches += one.launches;
+            stats->product_launches += one.product_launches;
+            stats->product_bytes += one.product_bytes;
+            stats->product_flops += one.product_flops;
+        }
+    };
+    // T host threads issue the launches in parallel (a solve is a few dozen short kernels,
+    // so one thread cannot keep the GPU busy): thread t takes matrices t, t + T, ... and
+    // alternates between its stream contexts t and t + T, finishing the older solve on a
+    // context before it reuses it.  Every solve is independent, so the results are those
+    // of single solves, whatever the threads' timing.
+    const int T = S < BKS_BATCH_THREADS ? S : BKS_BATCH_THREADS;
+    std::vector<bks_status> st_all(size_t(batch), BKS_OK);
+    std::vector<bks_stats> one_all(static_cast<size_t>(batch));
+    auto worker = [&](int t) {
+        DeviceGuard gd(ctx->device);
+        int owner[2] = {-1, -1};
+        bks_ctx* subs[2] = {ctx->subs[t], ctx->subs[t + T < S ? t + T : t]};
+        int r = 0;
+        for (int i = t; i < batch; i += T, ++r) {
+            const int h = subs[1] == subs[0] ? 0 : (r & 1);   // one context: finish before reuse
+            bks_ctx* sub = subs[h];
+            if (owner[h] >= 0) st_all[owner[h]] = finish_solve(sub, &one_all[owner[h]]);
+            owner[h] = -1;
+            const bks_status st_i = solve_entry(sub, &As[i], k, q, seeds ? seeds[i] : uint64_t(i),
+                                                pis ? pis[i] : nullptr, Zs[i], sigmas[i], Vs ? Vs[i] : nullptr,
+                                                opts, nullptr, krylov, triplets, true);
+            if (sub->pending.active) owner[h] = i;
+            else st_all[i] = st_i;
+        }
+        for (int h = 0; h < 2; ++h)
+            if (owner[h] >= 0) st_all[owner[h]] = finish_solve(subs[h], &one_all[owner[h]]);
+    };
+    run_workers(T, worker);
+    for (int i = 0; i < batch; ++i) note(i, st_all[i], one_all[i]);
+    batch_end(ctx, S, start);
+    if (worst != BKS_OK && worst != BKS_WARN_DEFLATED)
+        return fail(ctx, worst, "at least one matrix of the batch failed (see statuses)");
+    ctx->last_error.clear();
+    return worst;
+}
+
 }  // namespace
 
 namespace bks {
@@ -1208,104 +1337,60 @@ bks_status bks_block_krylov_batched(bks_ctx* ctx, int batch, const bks_matrix* A
                                     const uint64_t* seeds, const void* const* pis, void* const* Zs,
                                     void* const* sigmas, void* const* Vs, const bks_opts* opts,
                                     bks_stats* stats, bks_status* statuses) {
+    return batched_solve(ctx, batch, As, k, q, seeds, pis, Zs, sigmas, Vs, opts, stats, statuses, true, false,
+                         "bks_block_krylov_batched");
+}
+
+bks_status bks_ritz_triplets_batched(bks_ctx* ctx, int batch, const bks_matrix* As, int k, int q,
+                                     const uint64_t* seeds, const void* const* pis, int method, void* const* Us,
+                                     void* const* sigmas, void* const* Vs, const bks_opts* opts,
+                                     bks_status* statuses) {
     if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
-    if (batch < 0 || (batch > 0 && (As == nullptr || Zs == nullptr || sigmas == nullptr)))
-        return fail(ctx, BKS_ERR_INVALID_ARG, "bad bks_block_krylov_batched arguments");
-    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (method != 0 && method != 1) return fail(ctx, BKS_ERR_INVALID_ARG, "method must be 0 (BKI) or 1 (SI)");
+    if (batch > 0 && Vs == nullptr) return fail(ctx, BKS_ERR_INVALID_ARG, "Vs is required for the Ritz triplets");
+    for (int i = 0; i < batch && Vs != nullptr; ++i)
+        if (Vs[i] == nullptr) return fail(ctx, BKS_ERR_INVALID_ARG, "Vs is required for the Ritz triplets");
+    return batched_solve(ctx, batch, As, k, q, seeds, pis, Us, sigmas, Vs, opts, nullptr, statuses, method == 0,
+                         true, "bks_ritz_triplets_batched");
+}
+
+bks_status bks_backward_batched(bks_ctx* ctx, int dtype, int batch, const int64_t* ns, const int64_t* ds, int k,
+                                const int* ws, const void* const* Us, const void* const* sigmas,
+                                const void* const* Vs, const void* const* g_sigmas, const void* const* Gs,
+                                void* const* dAs, double gap_tau, bks_status* statuses) {
+    if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
+    if (batch < 0 || (batch > 0 && (ns == nullptr || ds == nullptr || ws == nullptr || Us == nullptr ||
+                                    sigmas == nullptr || Vs == nullptr || dAs == nullptr ||
+                                    (g_sigmas == nullptr && Gs == nullptr))))
+        return fail(ctx, BKS_ERR_INVALID_ARG, "bad bks_backward_batched arguments");
     if (batch == 0) return BKS_OK;
     DeviceGuard g(ctx->device);
     const int S = batch < BKS_BATCH_STREAMS ? batch : BKS_BATCH_STREAMS;
-    while (int(ctx->subs.size()) < S) {
-        bks_ctx* sub = nullptr;
-        bks_status cs = bks_create(&sub, ctx->device);
-        if (cs != BKS_OK) return fail(ctx, cs, "could not create a stream context for the batch");
-        if (cudaStreamCreateWithFlags(&sub->stream, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();
-            bks_destroy(sub);
-            return fail(ctx, BKS_ERR_CUDA, "could not create a stream for the batch");
-        }
-        sub->own_stream = true;
-        ctx->subs.push_back(sub);
-    }
-    {   // size every stream's workspace for the largest matrix once (no reallocation mid-batch)
-        size_t need = 0;
-        for (int i = 0; i < batch; ++i) {
-            size_t b = 0;
-            if (bks_workspace_size(&As[i], k, q, 0, opts, &b) == BKS_OK && b > need) need = b;
-        }
-        for (int j = 0; j < S; ++j)
-            if (need > 0 && ensure_ws(ctx->subs[j], need) != BKS_OK)
-                return fail(ctx, BKS_ERR_NOMEM, "could not allocate the batch workspaces");
-    }
-    // the batch starts after the work already queued on the caller's stream
-    cudaEvent_t start;
-    cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
-    cudaEventRecord(start, ctx->stream);
-    for (int j = 0; j < S; ++j) cudaStreamWaitEvent(ctx->subs[j]->stream, start, 0);
-    bks_status worst = BKS_OK;
-    auto note = [&](int i, bks_status st_i, const bks_stats& one) {
-        if (statuses) statuses[i] = st_i;
-        if (st_i != BKS_OK && (worst == BKS_OK || (worst == BKS_WARN_DEFLATED && st_i != BKS_WARN_DEFLATED)))
-            worst = st_i;
-        if (stats) {
-            stats->q_eff = one.q_eff;
-            stats->width = one.width;
-            stats->jacobi_sweeps = one.jacobi_sweeps > stats->jacobi_sweeps ? one.jacobi_sweeps : stats->jacobi_sweeps;
-            stats->chol_shifts += one.chol_shifts;
-            stats->launches += one.launches;
-            stats->product_launches += one.product_launches;
-            stats->product_bytes += one.product_bytes;
-            stats->product_flops += one.product_flops;
-        }
-    };
-    // T host threads issue the launches in parallel (a solve is a few dozen short kernels,
-    // so one thread cannot keep the GPU busy): thread t takes matrices t, t + T, ... and
-    // alternates between its stream contexts t and t + T, finishing the older solve on a
-    // context before it reuses it.  Every solve is independent, so the results are those
-    // of single solves, whatever the threads' timing.
+    bks_status cs = ensure_subs(ctx, S);
+    if (cs != BKS_OK) return cs;
+    cudaEvent_t start = batch_begin(ctx, S);
+    // thread t takes matrices t, t + T, ... on its stream contexts t and t + T in turn (each
+    // backward synchronises its own stream); every gradient is that of a single call
     const int T = S < BKS_BATCH_THREADS ? S : BKS_BATCH_THREADS;
     std::vector<bks_status> st_all(size_t(batch), BKS_OK);
-    std::vector<bks_stats> one_all(static_cast<size_t>(batch));
     auto worker = [&](int t) {
         DeviceGuard gd(ctx->device);
-        int owner[2] = {-1, -1};
         bks_ctx* subs[2] = {ctx->subs[t], ctx->subs[t + T < S ? t + T : t]};
         int r = 0;
-        for (int i = t; i < batch; i += T, ++r) {
-            const int h = subs[1] == subs[0] ? 0 : (r & 1);   // one context: finish before reuse
-            bks_ctx* sub = subs[h];
-            if (owner[h] >= 0) st_all[owner[h]] = finish_solve(sub, &one_all[owner[h]]);
-            owner[h] = -1;
-            const bks_status st_i = solve_entry(sub, &As[i], k, q, seeds ? seeds[i] : uint64_t(i),
-                                                pis ? pis[i] : nullptr, Zs[i], sigmas[i], Vs ? Vs[i] : nullptr,
-                                                opts, nullptr, true, false, true);
-            if (sub->pending.active) owner[h] = i;
-            else st_all[i] = st_i;
-        }
-        for (int h = 0; h < 2; ++h)
-            if (owner[h] >= 0) st_all[owner[h]] = finish_solve(subs[h], &one_all[owner[h]]);
+        for (int i = t; i < batch; i += T, ++r)
+            st_all[i] = bks_backward(subs[r & 1], dtype, ns[i], ds[i], k, ws[i], Us[i], sigmas[i], Vs[i],
+                                     g_sigmas ? g_sigmas[i] : nullptr, Gs ? Gs[i] : nullptr, dAs[i], gap_tau);
     };
-    tc::encode_fn();   // the tensor-map encoder's one-time lookup, before the threads start
-    std::vector<std::thread> threads;
-    int started = 0;   // threads 1 .. started run concurrently; the rest run here
-    try {
-        for (int t = 1; t < T; ++t, ++started) threads.emplace_back(worker, t);
-    } catch (...) {
+    run_workers(T, worker);
+    batch_end(ctx, S, start);
+    bks_status worst = BKS_OK;
+    for (int i = 0; i < batch; ++i) {
+        if (statuses) statuses[i] = st_all[i];
+        if (st_all[i] != BKS_OK && worst == BKS_OK) worst = st_all[i];
     }
-    worker(0);
-    for (int t = started + 1; t < T; ++t) worker(t);
-    for (std::thread& th : threads) th.join();
-    for (int i = 0; i < batch; ++i) note(i, st_all[i], one_all[i]);
-    for (int j = 0; j < S; ++j) {
-        // later work on the caller's stream is ordered after the batch
-        cudaEventRecord(start, ctx->subs[j]->stream);
-        cudaStreamWaitEvent(ctx->stream, start, 0);
-    }
-    cudaEventDestroy(start);
-    if (worst != BKS_OK && worst != BKS_WARN_DEFLATED)
-        return fail(ctx, worst, "at least one matrix of the batch failed (see statuses)");
+    if (worst != BKS_OK) return fail(ctx, worst, "at least one matrix of the batch failed (see statuses)");
     ctx->last_error.clear();
-    return worst;
+    return BKS_OK;
 }
 
 bks_status bks_ritz_triplets(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t seed, const void* pi,

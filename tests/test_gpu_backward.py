@@ -100,3 +100,103 @@ def test_low_rank_reconstruction():
     assert np.max(np.abs(ak - ref)) < 1e-6 * np.max(np.abs(ref))
     # A_k = Z Z^T A
     assert np.max(np.abs(ak - un[:, :16] @ (un[:, :16].T @ a))) < 1e-5
+
+
+def loss_of(sk, ak, t):
+    return sk.sum() + ((ak - t) ** 2).sum()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_recompute_mode_is_bit_identical(dtype):
+    """recompute=True keeps only A and Pi between forward and backward and solves again in
+    the backward; the solve is deterministic, so the gradient is the same to the bit."""
+    a, t = case(300, 200, 21)
+    k, q = 16, 4
+    npdt = np.float64 if dtype == torch.float64 else np.float32
+    pi = cuda(synth.gaussian_pi(5, 200, k).astype(npdt), dtype)
+    grads = []
+    for rec in (False, True):
+        at = cuda(a, dtype).requires_grad_(True)
+        sk, ak = bk.rand_svd(at, k, q, pi=pi, recompute=rec)
+        loss_of(sk, ak, cuda(t, dtype)).backward()
+        grads.append(at.grad.clone())
+    assert torch.equal(grads[0], grads[1])
+
+
+def test_recompute_mode_keeps_no_triplets():
+    n, d, k, q = 2000, 1000, 16, 4
+    a = cuda(np.random.default_rng(5).standard_normal((n, d)), torch.float32)
+    w = bk.krylov_width(n, d, k, q)
+    held = {}
+    for rec in (False, True):
+        at = a.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        base = torch.cuda.memory_allocated()
+        sk, ak = bk.rand_svd(at, k, q, seed=3, recompute=rec)
+        torch.cuda.synchronize()
+        held[rec] = torch.cuda.memory_allocated() - base
+        del sk, ak
+    assert held[False] - held[True] >= (n + d + 1) * w * 4   # U, sigma and V are not held
+
+
+@pytest.mark.parametrize("recompute", [False, True])
+def test_batched_forward_backward_matches_oracle_and_single(recompute):
+    """Uneven shapes whose Krylov width covers min(n, d) (k = 16, q = 4: width 48, 64 or 80
+    after the cap), where the gradient is exact: every matrix's gradient matches the FP64
+    oracle's loss gradient, and the batched forward + backward equal the single calls bit
+    for bit."""
+    shapes = [(64, 48), (120, 64), (80, 200), (96, 80), (48, 300), (256, 64)]
+    k, q = 16, 4
+    mats, targets = [], []
+    for i, (n, d) in enumerate(shapes):
+        a, t = case(n, d, 700 + i)
+        mats.append(a)
+        targets.append(t)
+    pis = [cuda(synth.gaussian_pi(30 + i, d, k).astype(np.float64), torch.float64)
+           for i, (_, d) in enumerate(shapes)]
+    ats = [cuda(a, torch.float64).requires_grad_(True) for a in mats]
+    outs = bk.rand_svd_batched(ats, k, q, pis=pis, recompute=recompute)
+    sum(loss_of(sk, ak, cuda(t, torch.float64)) for (sk, ak), t in zip(outs, targets)).backward()
+    for i, (a, t) in enumerate(zip(mats, targets)):
+        g_ora = grad.loss_grad(a, k, t)
+        assert rel(ats[i].grad.cpu().numpy(), g_ora) < 1e-7, i
+        single = cuda(a, torch.float64).requires_grad_(True)
+        sk, ak = bk.rand_svd(single, k, q, pi=pis[i])
+        loss_of(sk, ak, cuda(t, torch.float64)).backward()
+        assert torch.equal(single.grad, ats[i].grad), i
+        assert torch.equal(sk, outs[i][0]) and torch.equal(ak, outs[i][1]), i
+
+
+def test_batched_uneven_workload_equals_single():
+    """Twelve FP32 matrices of the batched workload's shape ranges (m in [256, 4096], n in
+    [128, 2048]), seeds 0..11: the batched gradients equal the single calls' bit for bit."""
+    mats = synth.batched_planted(batch=12, seed=1005)
+    k, q = 16, 4
+    ts = [synth.loss_target(90 + i, *m.shape).astype(np.float32) for i, m in enumerate(mats)]
+    ats = [cuda(a, torch.float32).requires_grad_(True) for a in mats]
+    outs = bk.rand_svd_batched(ats, k, q)
+    sum(loss_of(sk, ak, cuda(t, torch.float32)) for (sk, ak), t in zip(outs, ts)).backward()
+    for i, (a, t) in enumerate(zip(mats, ts)):
+        single = cuda(a, torch.float32).requires_grad_(True)
+        sk, ak = bk.rand_svd(single, k, q, seed=i)
+        loss_of(sk, ak, cuda(t, torch.float32)).backward()
+        assert torch.equal(single.grad, ats[i].grad), i
+
+
+@pytest.mark.parametrize("d", [512, 510])
+def test_backward_products_match_the_oracle_formula(d):
+    """FP32 backward at 1024 x d, k = 16, q = 4 (width 80, below the rank): the two passes
+    over G run on the tensor cores for d = 512 and on the CUDA cores for d = 510 (rows not
+    16-byte aligned).  Both match the oracle's formula evaluated in FP64 on the same
+    triplets; the FP32 error is amplified by 1 / (lambda_16 - lambda_17) in the c_ij terms."""
+    n, k, q = 1024, 16, 4
+    a, _ = case(n, d, 77)
+    at = cuda(a, torch.float32)
+    u, s, v = bk.ritz_triplets(at, k, q, seed=9)
+    rng = np.random.default_rng(8)
+    gs = rng.standard_normal(k)
+    gg = rng.standard_normal((n, d))
+    got = bk.backward(u, s, v, k, cuda(gs, torch.float32), cuda(gg, torch.float32)).double().cpu().numpy()
+    un, sn, vn = (x.double().cpu().numpy() for x in (u, s, v))
+    ref = grad.adjoint_from_triplets(un, sn, vn, k, gs, gg, gap_tau=1e-6)
+    assert rel(got, ref) < 1e-3
