@@ -342,6 +342,18 @@ bks_status bks_backward_batched(bks_ctx* ctx, int dtype, int batch, const int64_
 bks_status bks_low_rank(bks_ctx* ctx, int dtype, int64_t n, int64_t d, int r, const void* U,
                         int64_t ldu, const void* sigma, const void* V, int64_t ldv, void* out);
 
+/* ---- failure-path self-test ------------------------------------------------------- */
+
+/* Runs one of the library's bounded device-side waits on a condition that nothing
+ * satisfies, so that the failure path can be tested without a GPU fault: which = 0 waits
+ * on an mbarrier phase that no thread or copy completes (the wait of the tensor-core
+ * pipelines), which = 1 on a grid barrier that expects one more CTA than is launched (the
+ * barrier of the cooperative orthonormalisation kernels).  The wait gives up after its
+ * limit (1 s), the kernel returns normally and the call returns BKS_ERR_TIMEOUT; the
+ * context and the stream remain usable.  No counterpart in the paper.  Synchronises the
+ * context's stream. */
+bks_status bks_selftest_wait(bks_ctx* ctx, int which);
+
 /* ---- allocation-free variant ------------------------------------------------------ */
 
 /* bks_sym_eig without any device allocation.  The paper has no counterpart: this entry

@@ -83,6 +83,7 @@ SIGNATURES = {
     "bks_orthonormalize": (_I32, [_P, _I32, _I64, _I32, _I32, _P, _I64, _P, _I64]),
     "bks_sym_eig": (_I32, [_P, _I32, _I32, _P, _I64, _P, _P, _I64]),
     "bks_sym_eig_noalloc": (_I32, [_P, _I32, _I32, _P, _I64, _P, _P, _I64]),
+    "bks_selftest_wait": (_I32, [_P, _I32]),
     "bks_krylov_width": (_I32, [_I64, _I64, _I32, _I32, _I32]),
     "bks_block_krylov_batched": (_I32, [_P, _I32, ctypes.POINTER(BksMatrix), _I32, _I32, _P, _P, _P, _P, _P,
                                         ctypes.POINTER(BksOpts), ctypes.POINTER(BksStats), _P]),

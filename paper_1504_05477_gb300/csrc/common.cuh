@@ -193,6 +193,10 @@ OrthSizes orth_sizes(int64_t len_max, int64_t ld_max, int mmax, int c, int elem_
 // is non-null, row-major at Qr_out (pitch ldr).  False, launching nothing, when the
 // shapes do not fit.
 bool orth_tc_fits(int64_t len, int m, int c, int num_sms);
+// Failure-path self-test: one bounded wait (0: mbarrier, 1: grid barrier) on a condition
+// nothing satisfies; it gives up after its limit and ORs ST_TIMEOUT into *ex.status.
+// bar: two zeroed words of device scratch.  False for an unknown `which`.
+bool wait_selftest(Exec& ex, int which, unsigned* bar);
 size_t orth_tc_part_floats(int64_t len, int mmax, int c, int num_sms);
 bool orth_tc(Exec& ex, int64_t len, int64_t ld, const float* Qc, int m, const float* W, int c, float* Qout,
              const float* Qr, float* Qr_out, int64_t ldr, float* part, int64_t part_cap, float* cts, int64_t ldct,

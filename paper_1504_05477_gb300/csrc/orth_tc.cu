@@ -755,6 +755,28 @@ __global__ void __launch_bounds__(NT, 1)
 
 size_t smem_bytes() { return size_t(NKB_W) * TILE + HALF + 2 * STAGE + sizeof(Ctl) + 8 * 32 * 8 * 4 + 1024; }
 
+// Failure-path self-test of the two bounded waits every pipeline and cooperative kernel
+// here relies on, each on a condition that nothing satisfies: which = 0 an mbarrier phase
+// no thread or copy completes (tc::wait_bar, the TMA / MMA pipeline wait), which = 1 the
+// grid barrier with one more arrival expected than there are CTAs (grid_sync).  Both give
+// up after WAIT_NS and flag ST_TIMEOUT; the kernel then returns normally.
+__global__ void wait_selftest_kernel(int which, unsigned* bar, int* status) {
+    __shared__ Ctl ctl;
+    __shared__ uint64_t never;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&never, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (which == 0) {
+        if (threadIdx.x == 0) tc::wait_bar(&never, 0, &abort_flag, status);
+    } else {
+        grid_sync(&ctl, bar, gridDim.x + 1, status);
+    }
+}
+
 }  // namespace otc
 
 // Rows per CTA and CTAs of the tensor-core orthonormalisation for a block of length len.
@@ -826,6 +848,15 @@ bool orth_tc(Exec& ex, int64_t len, int64_t ld, const float* Qc, int m, const fl
         cudaGetLastError();
         return false;
     }
+    ex.launches++;
+    return true;
+}
+
+bool wait_selftest(Exec& ex, int which, unsigned* bar) {
+    if (which != 0 && which != 1) return false;
+    cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), ex.stream);
+    // two CTAs for the grid barrier: both are resident, neither reaches the target
+    otc::wait_selftest_kernel<<<which == 0 ? 1 : 2, 32, 0, ex.stream>>>(which, bar, ex.status);
     ex.launches++;
     return true;
 }

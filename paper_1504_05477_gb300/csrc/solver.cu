@@ -1324,6 +1324,30 @@ bks_status bks_simul_iter(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint6
     return solve_entry(ctx, A, k, q, seed, pi, Z, sigma, V, opts, stats, false);
 }
 
+bks_status bks_selftest_wait(bks_ctx* ctx, int which) {
+    if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
+    if (which != 0 && which != 1) return fail(ctx, BKS_ERR_INVALID_ARG, "which must be 0 or 1");
+    DeviceGuard g(ctx->device);
+    bks_status s = ensure_ws(ctx, 256);
+    if (s != BKS_OK) return s;
+    Exec ex;
+    ex.stream = ctx->stream;
+    ex.num_sms = ctx->num_sms;
+    ex.status = static_cast<int*>(ctx->ws);
+    unsigned* bar = reinterpret_cast<unsigned*>(static_cast<char*>(ctx->ws) + 64);
+    cudaMemsetAsync(ex.status, 0, 16, ctx->stream);
+    wait_selftest(ex, which, bar);
+    cudaError_t e = cudaMemcpyAsync(ctx->host_status, ex.status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bks_selftest_wait");
+    if (ctx->host_status[0] & ST_TIMEOUT)
+        return fail(ctx, BKS_ERR_TIMEOUT, which == 0 ? "an mbarrier wait gave up (self-test)"
+                                                    : "a grid-barrier wait gave up (self-test)");
+    ctx->last_error.clear();
+    return BKS_OK;
+}
+
 bks_status bks_block_lanczos(bks_ctx* ctx, const bks_matrix* A, int k, int q, int reorth, uint64_t seed,
                              const void* pi, void* Z, void* sigma, void* V, const bks_opts* opts,
                              bks_stats* stats) {
