@@ -377,7 +377,8 @@ def quality_records(w, dev):
     ||A - Z Z^T A||_2 / sigma_{k+1} of the timed workload (true singular values from the
     device SVD), BKI against SI iterations to eps = 0.01 on it (paper Sec. 7 counts the
     iterations each method needs), and the BF16 + refinement form against the all-FP32 form
-    on the dense 65536 x 16384 BF16 workload (ms per solve and spectral ratio of each)."""
+    on the dense 65536 x 16384 BF16 workload (ms per solve and spectral ratio of each), and the
+    FP64 eigen-solve of M against the default FP32 one at width 450 (ms, Ritz values)."""
     import numpy as np
     import torch
 
@@ -395,6 +396,15 @@ def quality_records(w, dev):
     out["spectral_ratio_note"] = ("||A - Z Z^T A||_2 / sigma_{k+1} of a timed-configuration solve (seed 100); "
                                   "sigma from the eigenvalues of A^T A in FP64, the norm by a block Krylov "
                                   "estimate on the residual")
+    # eigen-solve of M in FP64 (opts.eig_f64) against the default FP32 tridiagonal path
+    z64, s64 = bk.block_krylov(a, k, w.q, seed=100, eig_f64=True)
+    _, s32 = bk.block_krylov(a, k, w.q, seed=100)
+    out["eig_f64"] = {
+        "width_450": {"ms_per_solve_fp32_eig": _event_ms(lambda: bk.block_krylov(a, k, w.q, seed=100), 3),
+                      "ms_per_solve_fp64_eig": _event_ms(lambda: bk.block_krylov(a, k, w.q, seed=100,
+                                                                                  eig_f64=True), 3),
+                      "max_rel_sigma_diff": float(((s64.double() - s32.double()).abs() / s32.double()).max()),
+                      "spectral_ratio_fp64_eig": _spectral(a, z64) / float(sig[k])}}
     iters, ratios = {}, {}
     for name, fn in (("block_krylov", bk.block_krylov), ("simul_iter", bk.simul_iter)):
         iters[name] = None
@@ -423,6 +433,9 @@ def quality_records(w, dev):
         z, _ = bk.block_krylov(ab, kk, qq, seed=7, **kw)
         rec[form] = {"ms_per_solve": ms, "spectral_ratio": _spectral(af, z) / s_k1}
     out["bf16_vs_f32"] = rec
+    out["eig_f64"]["width_700_bf16_refined"] = (
+        "unsupported: the FP64 one-sided Jacobi keeps M in one cluster's shared memory, which holds "
+        "widths up to 512 in FP64 (700 x 700 x 8 bytes do not fit)")
     del af, ab
     torch.cuda.empty_cache()
     return out

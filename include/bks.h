@@ -103,7 +103,11 @@ typedef struct {
                                    (BKI) or p (SI), q capped so that w <= min(n, d); a caller-
                                    supplied Pi is d x p.  Must be 0 or in [k, min(n, d)], at
                                    most 128; Ritz triplets take p = k */
-    int32_t reserved[3];
+    int32_t eig_f64;            /* FP32 and BF16 precisions: 1 solves the eigen-problem of M in FP64
+                                   (M formed as usual, then the one-sided Jacobi in FP64 and the
+                                   eigenvectors rounded to FP32); 0 (default) in FP32.  Widths up to
+                                   512 (BKS_ERR_UNSUPPORTED beyond).  Ignored on the FP64 path */
+    int32_t reserved[2];
 } bks_opts;
 
 typedef struct {
@@ -123,7 +127,8 @@ typedef struct {
                                    dominant product kernel alone (dense FP32: the tensor-core
                                    kernel; BF16: its BF16-rounded products; CSR: the SpMM) */
     int32_t product_kernel_launches;
-    int32_t eig_path;           /* eigen-solve that ran: 0 one-sided Jacobi, 1 tridiagonal */
+    int32_t eig_path;           /* eigen-solve that ran: 0 one-sided Jacobi, 1 tridiagonal, 2 the
+                                   one-sided Jacobi in FP64 (opts.eig_f64) */
     int32_t reserved[5];
 } bks_stats;
 

@@ -153,7 +153,8 @@ def _as_bks(a, precision="auto"):
 
 
 def _opts(precision="auto", basis_only=False, sign_fix=True, profile=False, jacobi_tol=0.0,
-          jacobi_max_sweeps=40, refine=True, simt=False, rr_mode="auto", eig_mode="auto", block_p=0):
+          jacobi_max_sweeps=40, refine=True, simt=False, rr_mode="auto", eig_mode="auto", block_p=0,
+          eig_f64=False):
     o = BksOpts()
     B.load().bks_opts_default(ctypes.byref(o))
     o.precision = {"auto": B.PREC_AUTO, "f64": B.PREC_F64, "f32": B.PREC_F32,
@@ -168,6 +169,7 @@ def _opts(precision="auto", basis_only=False, sign_fix=True, profile=False, jaco
     o.rr_mode = {"auto": 0, "qr": 1, "gram": 2}[rr_mode]
     o.eig_mode = {"auto": 0, "jacobi": 1}[eig_mode]
     o.block_p = int(block_p)
+    o.eig_f64 = int(eig_f64)
     return o
 
 

@@ -35,7 +35,7 @@ class BksOpts(ctypes.Structure):
         ("sign_fix", ctypes.c_int32), ("jacobi_max_sweeps", ctypes.c_int32),
         ("jacobi_tol", ctypes.c_double), ("profile", ctypes.c_int32),
         ("product_path", ctypes.c_int32), ("rr_mode", ctypes.c_int32), ("eig_mode", ctypes.c_int32),
-        ("block_p", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
+        ("block_p", ctypes.c_int32), ("eig_f64", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
     ]
 
 

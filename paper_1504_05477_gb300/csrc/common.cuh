@@ -244,6 +244,10 @@ void sign_fix(Exec& ex, T* Z, int64_t n, int k, int64_t ldz, T* Ut, int64_t w, i
 template <typename T>
 void row_norms(Exec& ex, T* Vt, int k, int64_t len, int64_t ldv, T* sigma, bool normalise);
 
+// dst (rows x cols, row pitch ldd) = src (row pitch lds), converted element by element.
+template <typename TS, typename TD>
+void cast_2d(Exec& ex, const TS* src, int64_t rows, int64_t cols, int64_t lds, TD* dst, int64_t ldd);
+
 // Scan `n` values for non-finite entries, OR-ing ST_NONFINITE into the status word.
 template <typename T>
 void check_finite(Exec& ex, const T* x, int64_t n);

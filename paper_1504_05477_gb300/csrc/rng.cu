@@ -181,6 +181,27 @@ void transpose_in(Exec& ex, const void* src, int src_dtype, int64_t rows, int64_
     ex.launches++;
 }
 
+template <typename TS, typename TD>
+__global__ void cast_2d_kernel(const TS* __restrict__ src, int64_t rows, int64_t cols, int64_t lds,
+                               TD* __restrict__ dst, int64_t ldd) {
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < rows * cols;
+         e += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t r = e / cols, c = e % cols;
+        dst[r * ldd + c] = TD(src[r * lds + c]);
+    }
+}
+
+template <typename TS, typename TD>
+void cast_2d(Exec& ex, const TS* src, int64_t rows, int64_t cols, int64_t lds, TD* dst, int64_t ldd) {
+    int64_t blocks = (rows * cols + 255) / 256;
+    if (blocks > 8 * int64_t(ex.num_sms)) blocks = 8 * int64_t(ex.num_sms);
+    if (blocks < 1) blocks = 1;
+    cast_2d_kernel<TS, TD><<<unsigned(blocks), 256, 0, ex.stream>>>(src, rows, cols, lds, dst, ldd);
+    ex.launches++;
+}
+template void cast_2d<float, double>(Exec&, const float*, int64_t, int64_t, int64_t, double*, int64_t);
+template void cast_2d<double, float>(Exec&, const double*, int64_t, int64_t, int64_t, float*, int64_t);
+
 template <typename T>
 void check_finite(Exec& ex, const T* x, int64_t n) {
     int blocks = int((n + 255) / 256);

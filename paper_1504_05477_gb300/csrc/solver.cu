@@ -302,7 +302,8 @@ struct Plan {
     CsrLayout csr;
     size_t td, td_bytes;     // scratch of the tridiagonal eigen-solve (0 bytes when it cannot run)
     size_t Qt, Bt, QBt, Pit, W, Wtmp, Wb, Wbtmp, part, og, rfac, ct, Rm, JX, lam, nrm, Vt,
-        order, Vk, stat, fpart, fgram, fbar, otc_part, otc_cts, otc_h, otc_bar, qr, vtp, zt, cf;
+        order, Vk, stat, fpart, fgram, fbar, otc_part, otc_cts, otc_h, otc_bar, qr, vtp, zt, cf, Md, JXd, lamd,
+        nrmd, Vtd;
     int64_t ldvt;         // row pitch of the padded copy of the Ritz coefficients (vtp)
     int64_t ldcf;         // row pitch of the Block Lanczos coefficients C_j (k x 2k)
     int64_t fcap, otc_cap, otc_ldct, ldr;
@@ -328,7 +329,7 @@ int64_t max_partials(int64_t n, int64_t d, int k, int w, int sms) {
     return p;
 }
 
-Plan make_plan(const bks_matrix* A, int k, int q_eff, int w, size_t tb, int sms, int kout) {
+Plan make_plan(const bks_matrix* A, int k, int q_eff, int w, size_t tb, int sms, int kout, bool eig_f64) {
     const int64_t n = A->n, d = A->d;
     Plan p{};
     p.n = n; p.d = d; p.k = k; p.q = q_eff; p.w = w;
@@ -378,6 +379,13 @@ Plan make_plan(const bks_matrix* A, int k, int q_eff, int w, size_t tb, int sms,
     p.Vk = a.take(size_t(kout) * p.ldd * tb);
     p.ldcf = round_up(2 * k, 32);
     p.cf = a.take(size_t(k) * p.ldcf * tb);
+    // FP64 eigen-solve of M on the FP32 path: M, the Jacobi scratch and U in FP64
+    const size_t e64 = (tb == 4 && eig_f64) ? 8 : 0;
+    p.Md = a.take(size_t(w) * w * e64);
+    p.JXd = a.take(size_t(w) * w * e64);
+    p.lamd = a.take(size_t(w) * e64);
+    p.nrmd = a.take(size_t(w) * e64);
+    p.Vtd = a.take(size_t(w) * w * e64);
     // FP32: Z = Q Ubar_k and B Ubar_k on the tensor cores, from a copy of the coefficients
     // with a 128-byte row pitch, through Z^T (kout x ldn)
     p.ldvt = round_up(w, 32);
@@ -518,9 +526,12 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
         if (!o.basis_only && !jacobi_plan(w, int(sizeof(T)), C, b, E, sm))
             return fail(ctx, BKS_ERR_UNSUPPORTED,
                         "Krylov width " + std::to_string(w) + " exceeds the Jacobi solver's limit");
+        if (sizeof(T) == 4 && o.eig_f64 && !o.basis_only && !jacobi_plan(w, 8, C, b, E, sm))
+            return fail(ctx, BKS_ERR_UNSUPPORTED,
+                        "Krylov width " + std::to_string(w) + " exceeds the FP64 Jacobi solver's limit");
     }
     const int kout = triplets ? w : kz;   // Ritz vectors returned
-    Plan p = make_plan(A, k, q_eff, w, sizeof(T), ctx->num_sms, kout);
+    Plan p = make_plan(A, k, q_eff, w, sizeof(T), ctx->num_sms, kout, o.eig_f64 != 0);
     bks_status s = ensure_ws(ctx, p.total);
     if (s != BKS_OK) return s;
     char* base = static_cast<char*>(ctx->ws);
@@ -860,9 +871,24 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
         check_finite<T>(ex, Rm, int64_t(wr) * wr);
         // a6: eigen-decomposition of M, descending (row j of Rm is column j of R^T)
         const int sweeps = o.jacobi_max_sweeps > 0 ? o.jacobi_max_sweeps : 40;
-        eig_path = use_td && tridiag_fits<T>(wr, kz) && topk_tridiag<T>(ex, wr, Rm, kz, Vt, wr, reinterpret_cast<T*>(base + p.td), ows) ? 1 : 0;
-        if (eig_path == 0)
-            sym_eig<T>(ex, wr, Rm, wr, JX, wr, lam, nrm, Vt, wr, order, sweeps, o.jacobi_tol, stat + 1);
+        if (sizeof(T) == 4 && o.eig_f64) {
+            // FP64 eigen-solve of M (one-sided Jacobi), eigenvectors rounded to FP32
+            double* Md = reinterpret_cast<double*>(base + p.Md);
+            double* Vtd = reinterpret_cast<double*>(base + p.Vtd);
+            cast_2d<float, double>(ex, reinterpret_cast<const float*>(Rm), wr, wr, wr, Md, wr);
+            sym_eig<double>(ex, wr, Md, wr, reinterpret_cast<double*>(base + p.JXd), wr,
+                            reinterpret_cast<double*>(base + p.lamd), reinterpret_cast<double*>(base + p.nrmd), Vtd,
+                            wr, order, sweeps, o.jacobi_tol, stat + 1);
+            cast_2d<double, float>(ex, Vtd, kout, wr, wr, reinterpret_cast<float*>(Vt), wr);
+            eig_path = 2;
+        } else {
+            eig_path = use_td && tridiag_fits<T>(wr, kz) &&
+                               topk_tridiag<T>(ex, wr, Rm, kz, Vt, wr, reinterpret_cast<T*>(base + p.td), ows)
+                           ? 1
+                           : 0;
+            if (eig_path == 0)
+                sym_eig<T>(ex, wr, Rm, wr, JX, wr, lam, nrm, Vt, wr, order, sweeps, o.jacobi_tol, stat + 1);
+        }
         // a7: Z = Q Ubar_k (row-major n x k).  FP32: on the tensor cores as
         // Z^T = (Q_array^T X)^T with X = Ubar_k^T (rows of Vt, copied to a 128-byte pitch),
         // then transposed; otherwise the CUDA-core kernel writes Z directly
@@ -1299,7 +1325,7 @@ bks_status bks_workspace_size(const bks_matrix* A, int k, int q, int method, con
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaGetLastError();
-    *bytes = make_plan(A, k, q_eff, w, tb, sms, w).total;   // enough for the Ritz triplets too
+    *bytes = make_plan(A, k, q_eff, w, tb, sms, w, o.eig_f64 != 0).total;   // enough for the Ritz triplets too
     return BKS_OK;
 }
 
