@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--block-p", type=int, default=0,
                    help="p >= k columns in Pi and in every Krylov block (Sec. 8); 0 = k")
     p.add_argument("--q", type=int, default=None, help="iteration count (default: the workload's)")
+    p.add_argument("--max-sms", type=int, default=None,
+                   help="SMs each solve's kernels spread over (bks_opts.max_sms; default: the library's choice)")
     p.add_argument("--adapt-tol", type=float, default=0.0,
                    help="Block Krylov with q chosen on the fly (at most q): stop once no leading Ritz "
                         "value moves by more than this (relative) between iterations")
@@ -480,6 +482,8 @@ def main():
         w.q = args.q
     if args.block_p:
         w.solve_kw["block_p"] = args.block_p
+    if args.max_sms is not None:
+        w.solve_kw["max_sms"] = args.max_sms
     if args.adapt_tol > 0:
         import paper_1504_05477_gb300 as bk
         tol = args.adapt_tol
@@ -592,6 +596,8 @@ def main():
               "k": w.k, "q": w.q, "width": width, "parallelism": f"replicas x{world}", "l2": w.l2}
     if args.block_p:
         config["block_p"] = args.block_p
+    if args.max_sms is not None:
+        config["max_sms"] = args.max_sms
     if args.adapt_tol > 0:
         config["adapt_tol"] = args.adapt_tol
         config["q"] = f"adaptive, at most {w.q}"

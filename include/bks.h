@@ -107,7 +107,12 @@ typedef struct {
                                    (M formed as usual, then the one-sided Jacobi in FP64 and the
                                    eigenvectors rounded to FP32); 0 (default) in FP32.  Widths up to
                                    512 (BKS_ERR_UNSUPPORTED beyond).  Ignored on the FP64 path */
-    int32_t reserved[2];
+    int32_t max_sms;            /* SMs the call's kernels spread over (grid sizes of the products,
+                                   orthonormalisations and reductions); 0 = all.  Results depend on
+                                   it in the last bits (summation orders follow the grid).  Batched
+                                   calls: 0 lets the call choose per shape class (see
+                                   bks_block_krylov_batched); a value > 0 applies to every matrix */
+    int32_t reserved[1];
 } bks_opts;
 
 typedef struct {
@@ -279,8 +284,12 @@ bks_status bks_sym_eig(bks_ctx* ctx, int dtype, int w, const void* M, int64_t ld
  * seed i) or pis[i] (NULL array, or NULL entries: generate from the seed) give the start
  * blocks.  The solves run on up to 16 streams of the context (created on first use),
  * launched from up to 8 host threads, so several are in flight at once; each result is
- * that of the single solve.  The batch is ordered after the work already on the
- * context's stream, and later work on that stream after the batch.  statuses[i] (host,
+ * that of the single call made with the batch's opts.max_sms (below).  The batch is
+ * ordered after the work already on the
+ * context's stream, and later work on that stream after the batch.  Each solve's kernels
+ * spread over opts.max_sms SMs; with max_sms = 0 the budget cached by bks_batched_autotune
+ * for this batch's signature, else an eighth of the SMs, so that several latency-bound
+ * solves share the GPU.  statuses[i] (host,
  * may be NULL) receives each solve's status; the return value is the first error, else
  * BKS_WARN_DEFLATED if any solve was capped, else BKS_OK.  stats (may be NULL) sums
  * launches, product bytes and flops over the batch.  Synchronises the streams. */
@@ -288,6 +297,25 @@ bks_status bks_block_krylov_batched(bks_ctx* ctx, int batch, const bks_matrix* A
                                     const uint64_t* seeds, const void* const* pis, void* const* Zs,
                                     void* const* sigmas, void* const* Vs, const bks_opts* opts,
                                     bks_stats* stats, bks_status* statuses);
+
+/* Chooses the SM budget (bks_opts.max_sms) of bks_block_krylov_batched for this batch: runs
+ * the batch once per candidate (1/16, 1/8, 1/4, 1/2 and all of the GPU's SMs per solve, after
+ * a warm-up pass), keeps the fastest, caches it in the context under the batch's signature
+ * (k, q, and the multiset of the matrices' shape classes: kind, dtype, ceil log2 of n and d)
+ * and leaves in Zs / sigmas / Vs the results computed with it.  Later batched calls with
+ * opts.max_sms = 0 and the same signature use the cached budget; batches never tuned use an
+ * eighth of the SMs.  *best_max_sms (may be NULL) receives the budget, *best_ms (may be NULL)
+ * its time for the whole batch.  Arguments otherwise as bks_block_krylov_batched. */
+bks_status bks_batched_autotune(bks_ctx* ctx, int batch, const bks_matrix* As, int k, int q,
+                                const uint64_t* seeds, const void* const* pis, void* const* Zs,
+                                void* const* sigmas, void* const* Vs, const bks_opts* opts,
+                                int* best_max_sms, float* best_ms);
+
+/* The SM budget a batched solve (method 0 BKI, 1 SI) with opts.max_sms = 0 would use for
+ * this batch: the one cached by bks_batched_autotune for its signature, else an eighth of
+ * the SMs.  A single call with opts.max_sms set to it reproduces a batch member bit for bit.
+ * 0 for bad arguments. */
+int bks_batch_budget(const bks_ctx* ctx, int batch, const bks_matrix* As, int k, int q, int method);
 
 /* Krylov width w of a solve: k(q_eff + 1) for Block Krylov (method 0; q capped so that
  * w <= min(n, d), Sec. 4), k for Simultaneous Iteration (method 1).  0 for bad sizes. */
@@ -306,8 +334,8 @@ bks_status bks_ritz_triplets(bks_ctx* ctx, const bks_matrix* A, int k, int q, ui
  * forward and backward): for each i, as bks_ritz_triplets on As[i], Us[i] (n_i x w_i),
  * sigmas[i] (w_i) and Vs[i] (d_i x w_i), w_i = bks_krylov_width(n_i, d_i, k, q, method).
  * Streams, host threads, seeds, pis, statuses and the return value as for
- * bks_block_krylov_batched; every result is that of the single call.  Synchronises the
- * streams. */
+ * bks_block_krylov_batched (the SM budget included); every result is that of the single
+ * call made with the same opts.max_sms.  Synchronises the streams. */
 bks_status bks_ritz_triplets_batched(bks_ctx* ctx, int batch, const bks_matrix* As, int k, int q,
                                      const uint64_t* seeds, const void* const* pis, int method,
                                      void* const* Us, void* const* sigmas, void* const* Vs,

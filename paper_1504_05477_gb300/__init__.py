@@ -16,7 +16,7 @@ from ._binding import BksError, BksMatrix, BksOpts, BksStats  # noqa: F401
 
 __all__ = ["block_krylov", "block_krylov_adaptive", "block_lanczos", "simul_iter", "matmul", "orthonormalize", "sym_eig", "gen_pi", "CsrMatrix",
            "ritz_triplets", "low_rank", "backward", "rand_svd", "krylov_width", "block_krylov_batched",
-           "ritz_triplets_batched", "backward_batched", "rand_svd_batched",
+           "ritz_triplets_batched", "backward_batched", "rand_svd_batched", "batch_budget", "batched_autotune",
            "gen_pi_host", "Context", "context", "dense_matrix", "BksError", "lib_path"]
 
 
@@ -154,7 +154,7 @@ def _as_bks(a, precision="auto"):
 
 def _opts(precision="auto", basis_only=False, sign_fix=True, profile=False, jacobi_tol=0.0,
           jacobi_max_sweeps=40, refine=True, simt=False, rr_mode="auto", eig_mode="auto", block_p=0,
-          eig_f64=False):
+          eig_f64=False, max_sms=0):
     o = BksOpts()
     B.load().bks_opts_default(ctypes.byref(o))
     o.precision = {"auto": B.PREC_AUTO, "f64": B.PREC_F64, "f32": B.PREC_F32,
@@ -170,6 +170,7 @@ def _opts(precision="auto", basis_only=False, sign_fix=True, profile=False, jaco
     o.eig_mode = {"auto": 0, "jacobi": 1}[eig_mode]
     o.block_p = int(block_p)
     o.eig_f64 = int(eig_f64)
+    o.max_sms = int(max_sms)
     return o
 
 
@@ -407,8 +408,9 @@ def _autograd_function():
         same deterministic solve, which then holds only A and Pi."""
 
         @staticmethod
-        def forward(ctx, a, k, q, seed, pi, method, precision, gap_tau, recompute):
-            u, s, v = ritz_triplets(a.detach(), k, q, seed=seed, pi=pi, method=method, precision=precision)
+        def forward(ctx, a, k, q, seed, pi, method, precision, gap_tau, recompute, max_sms):
+            u, s, v = ritz_triplets(a.detach(), k, q, seed=seed, pi=pi, method=method, precision=precision,
+                                    max_sms=max_sms)
             if recompute:
                 if pi is not None:
                     ctx.save_for_backward(a, pi)
@@ -417,7 +419,7 @@ def _autograd_function():
             else:
                 ctx.save_for_backward(u, s, v)
             ctx.k, ctx.q, ctx.seed, ctx.method, ctx.precision = k, q, seed, method, precision
-            ctx.gap_tau, ctx.in_dtype, ctx.recompute = gap_tau, a.dtype, recompute
+            ctx.gap_tau, ctx.in_dtype, ctx.recompute, ctx.max_sms = gap_tau, a.dtype, recompute, max_sms
             return s[:k].clone(), low_rank(u, s, v, k)
 
         @staticmethod
@@ -426,21 +428,21 @@ def _autograd_function():
                 saved = ctx.saved_tensors
                 a, pi = saved[0], (saved[1] if len(saved) > 1 else None)
                 u, s, v = ritz_triplets(a.detach(), ctx.k, ctx.q, seed=ctx.seed, pi=pi, method=ctx.method,
-                                        precision=ctx.precision)
+                                        precision=ctx.precision, max_sms=ctx.max_sms)
             else:
                 u, s, v = ctx.saved_tensors
             da = backward(u, s, v, ctx.k, g_sigma, g_ak, ctx.gap_tau)
-            return da.to(ctx.in_dtype), None, None, None, None, None, None, None, None
+            return da.to(ctx.in_dtype), None, None, None, None, None, None, None, None, None
 
     class RandSVDBatched(torch.autograd.Function):
         """rand_svd on a list of matrices: one batched triplets call forward, one batched
         backward call (bks_ritz_triplets_batched, bks_backward_batched)."""
 
         @staticmethod
-        def forward(ctx, k, q, seeds, pis, method, precision, gap_tau, recompute, *mats):
+        def forward(ctx, k, q, seeds, pis, method, precision, gap_tau, recompute, max_sms, *mats):
             trips = ritz_triplets_batched([m.detach() for m in mats], k, q, seeds=seeds, pis=pis, method=method,
-                                          precision=precision)
-            ctx.k, ctx.q, ctx.seeds, ctx.pis, ctx.method = k, q, seeds, pis, method
+                                          precision=precision, max_sms=max_sms)
+            ctx.k, ctx.q, ctx.seeds, ctx.pis, ctx.method, ctx.max_sms = k, q, seeds, pis, method, max_sms
             ctx.precision, ctx.gap_tau, ctx.recompute = precision, gap_tau, recompute
             ctx.in_dtypes = [m.dtype for m in mats]
             if recompute:
@@ -457,11 +459,12 @@ def _autograd_function():
             saved = ctx.saved_tensors
             if ctx.recompute:
                 trips = ritz_triplets_batched([m.detach() for m in saved], ctx.k, ctx.q, seeds=ctx.seeds,
-                                              pis=ctx.pis, method=ctx.method, precision=ctx.precision)
+                                              pis=ctx.pis, method=ctx.method, precision=ctx.precision,
+                                              max_sms=ctx.max_sms)
             else:
                 trips = [tuple(saved[3 * i:3 * i + 3]) for i in range(len(saved) // 3)]
             das = backward_batched(trips, ctx.k, list(grads[0::2]), list(grads[1::2]), ctx.gap_tau)
-            return (None,) * 8 + tuple(da.to(dt) for da, dt in zip(das, ctx.in_dtypes))
+            return (None,) * 9 + tuple(da.to(dt) for da, dt in zip(das, ctx.in_dtypes))
 
     return RandSVD, RandSVDBatched
 
@@ -469,7 +472,8 @@ def _autograd_function():
 _RANDSVD = None
 
 
-def rand_svd(a, k, q, seed=0, pi=None, method="bki", precision="auto", gap_tau=0.0, recompute=False):
+def rand_svd(a, k, q, seed=0, pi=None, method="bki", precision="auto", gap_tau=0.0, recompute=False,
+             max_sms=0):
     """Differentiable (Sigma_k, A_k) of Block Krylov (method "bki") or Simultaneous
     Iteration ("si") on a dense CUDA matrix.  recompute=True keeps no Ritz triplets between
     forward and backward (only A and Pi) and rebuilds them in the backward; the gradient is
@@ -477,11 +481,11 @@ def rand_svd(a, k, q, seed=0, pi=None, method="bki", precision="auto", gap_tau=0
     global _RANDSVD
     if _RANDSVD is None:
         _RANDSVD = _autograd_function()
-    return _RANDSVD[0].apply(a, k, q, seed, pi, method, precision, gap_tau, bool(recompute))
+    return _RANDSVD[0].apply(a, k, q, seed, pi, method, precision, gap_tau, bool(recompute), int(max_sms))
 
 
 def rand_svd_batched(mats, k, q, seeds=None, pis=None, method="bki", precision="auto", gap_tau=0.0,
-                     recompute=False):
+                     recompute=False, max_sms=0):
     """rand_svd on a list of dense CUDA matrices of any shapes, forward and backward each in
     one batched call.  Returns [(Sigma_k, A_k), ...], differentiable in every matrix."""
     global _RANDSVD
@@ -489,8 +493,54 @@ def rand_svd_batched(mats, k, q, seeds=None, pis=None, method="bki", precision="
         _RANDSVD = _autograd_function()
     if len(mats) == 0:
         return []
-    flat = _RANDSVD[1].apply(k, q, seeds, pis, method, precision, gap_tau, bool(recompute), *mats)
+    flat = _RANDSVD[1].apply(k, q, seeds, pis, method, precision, gap_tau, bool(recompute), int(max_sms), *mats)
     return [(flat[2 * i], flat[2 * i + 1]) for i in range(len(mats))]
+
+
+def batch_budget(mats, k, q, method="bki"):
+    """SMs per solve a batched call with max_sms = 0 uses for this batch (bks_batch_budget): the
+    budget batched_autotune cached for its signature, else an eighth of the GPU.  A single call
+    with max_sms set to it reproduces a batch member bit for bit."""
+    b = len(mats)
+    arr = (BksMatrix * b)()
+    dev = None
+    for i, a in enumerate(mats):
+        m, dv, _ = _as_bks(a)
+        dev = dv if dev is None else dev
+        arr[i] = m
+    ctx = context(dev)
+    return int(ctx.lib.bks_batch_budget(ctx.ptr, b, arr, int(k), int(q), 0 if method == "bki" else 1))
+
+
+def batched_autotune(mats, k, q, seeds=None, want_v=False, precision="auto", **kw):
+    """Times the batch at each candidate SM budget (bks_batched_autotune), caches the fastest for
+    batches of this signature and returns (results, budget, ms per batch)."""
+    torch = _torch()
+    b = len(mats)
+    arr = (BksMatrix * b)()
+    zp, sp, vp = ((ctypes.c_void_p * b)() for _ in range(3))
+    outs, dev = [], None
+    for i, a in enumerate(mats):
+        m, dv, odt = _as_bks(a, precision)
+        dev = dv if dev is None else dev
+        arr[i] = m
+        z = torch.empty((m.n, k), dtype=odt, device=dv)
+        s = torch.empty((k,), dtype=odt, device=dv)
+        v = torch.empty((m.d, k), dtype=odt, device=dv) if want_v else None
+        zp[i], sp[i] = z.data_ptr(), s.data_ptr()
+        if v is not None:
+            vp[i] = v.data_ptr()
+        outs.append((z, s, v) if want_v else (z, s))
+    ctx = context(dev)
+    seeds_arr = (ctypes.c_uint64 * b)(*[int(x) & (2**64 - 1) for x in (seeds if seeds is not None else range(b))])
+    opts = _opts(precision=precision, **kw)
+    best, ms = ctypes.c_int(0), ctypes.c_float(0.0)
+    B.check(ctx.lib.bks_batched_autotune(ctx.ptr, b, arr, int(k), int(q), ctypes.cast(seeds_arr, ctypes.c_void_p), None,
+                                         ctypes.cast(zp, ctypes.c_void_p), ctypes.cast(sp, ctypes.c_void_p),
+                                         ctypes.cast(vp, ctypes.c_void_p) if want_v else None, ctypes.byref(opts),
+                                         ctypes.byref(best), ctypes.byref(ms)),
+            ctx.ptr, "bks_batched_autotune")
+    return outs, best.value, ms.value
 
 
 def ritz_triplets_batched(mats, k, q, seeds=None, pis=None, method="bki", precision="auto", **kw):

@@ -35,7 +35,8 @@ class BksOpts(ctypes.Structure):
         ("sign_fix", ctypes.c_int32), ("jacobi_max_sweeps", ctypes.c_int32),
         ("jacobi_tol", ctypes.c_double), ("profile", ctypes.c_int32),
         ("product_path", ctypes.c_int32), ("rr_mode", ctypes.c_int32), ("eig_mode", ctypes.c_int32),
-        ("block_p", ctypes.c_int32), ("eig_f64", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2),
+        ("block_p", ctypes.c_int32), ("eig_f64", ctypes.c_int32), ("max_sms", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 1),
     ]
 
 
@@ -90,6 +91,9 @@ SIGNATURES = {
     "bks_ritz_triplets": (_I32, [_P, ctypes.POINTER(BksMatrix), _I32, _I32, _U64, _P, _I32, _P, _P, _P,
                                  ctypes.POINTER(BksOpts), ctypes.POINTER(BksStats)]),
     "bks_backward": (_I32, [_P, _I32, _I64, _I64, _I32, _I32, _P, _P, _P, _P, _P, _P, ctypes.c_double]),
+    "bks_batch_budget": (_I32, [_P, _I32, ctypes.POINTER(BksMatrix), _I32, _I32, _I32]),
+    "bks_batched_autotune": (_I32, [_P, _I32, ctypes.POINTER(BksMatrix), _I32, _I32, _P, _P, _P, _P, _P,
+                                    ctypes.POINTER(BksOpts), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
     "bks_ritz_triplets_batched": (_I32, [_P, _I32, ctypes.POINTER(BksMatrix), _I32, _I32, _P, _P, _I32, _P, _P,
                                          _P, ctypes.POINTER(BksOpts), _P]),
     "bks_backward_batched": (_I32, [_P, _I32, _I32, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P, ctypes.c_double,

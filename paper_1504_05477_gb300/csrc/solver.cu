@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -56,6 +57,7 @@ struct bks_ctx {
     std::string last_error;
     std::vector<cudaEvent_t> events;
     KernelLog klog;
+    std::map<std::string, int> batch_sms;   // SM budget per batch signature (bks_batched_autotune)
     ~bks_ctx() {
         for (int i = 0; i < klog.created; ++i) cudaEventDestroy(klog.ev[i]);
     }
@@ -593,7 +595,7 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
     Exec ex;
     ex.stream = ctx->stream;
     ex.status = stat;
-    ex.num_sms = ctx->num_sms;
+    ex.num_sms = o.max_sms > 0 && o.max_sms < ctx->num_sms ? o.max_sms : ctx->num_sms;
     if (o.profile) {
         ctx->klog.n = 0;
         ex.klog = &ctx->klog;
@@ -1022,6 +1024,7 @@ bks_status solve_entry(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t
         if (triplets && o.block_p != k)
             return fail(ctx, BKS_ERR_INVALID_ARG, "Ritz triplets are computed with block_p = k");
     }
+    if (o.max_sms < 0) return fail(ctx, BKS_ERR_INVALID_ARG, "max_sms must be >= 0");
     if (defer) o.profile = 0;
     if (prec == BKS_PREC_F64)
         return solve<double>(ctx, A, k, q, seed, pi, Z, sigma, V, o, st, krylov, triplets, defer, adapt_tol,
@@ -1033,6 +1036,25 @@ bks_status solve_entry(bks_ctx* ctx, const bks_matrix* A, int k, int q, uint64_t
 
 
 // ------------------------------------------------------------------- batches
+int default_batch_sms(int num_sms) { return num_sms / 8 > 8 ? num_sms / 8 : 8; }
+
+// Signature of a batch for the SM-budget cache: the solve (k, q, method, triplets) and the
+// multiset of its matrices' shape classes (kind, dtype, ceil log2 of n and of d).
+std::string batch_signature(int batch, const bks_matrix* As, int k, int q, bool krylov, bool triplets) {
+    auto lg = [](int64_t x) {
+        int l = 0;
+        while ((int64_t(1) << l) < x) ++l;
+        return l;
+    };
+    std::map<std::string, int> classes;
+    for (int i = 0; i < batch; ++i)
+        ++classes[std::to_string(As[i].kind) + "." + std::to_string(As[i].dtype) + "." + std::to_string(lg(As[i].n)) +
+                  "." + std::to_string(lg(As[i].d))];
+    std::string sig = std::to_string(k) + "/" + std::to_string(q) + "/" + (krylov ? "b" : "s") + (triplets ? "t" : "") + ":";
+    for (const auto& c : classes) sig += c.first + "x" + std::to_string(c.second) + ";";
+    return sig;
+}
+
 // Up to S stream contexts of ctx (created on first use, each with its own stream).
 bks_status ensure_subs(bks_ctx* ctx, int S) {
     while (int(ctx->subs.size()) < S) {
@@ -1107,6 +1129,16 @@ bks_status batched_solve(bks_ctx* ctx, int batch, const bks_matrix* As, int k, i
             if (need > 0 && ensure_ws(ctx->subs[j], need) != BKS_OK)
                 return fail(ctx, BKS_ERR_NOMEM, "could not allocate the batch workspaces");
     }
+    // SMs per solve: the caller's opts.max_sms, else the budget bks_batched_autotune cached
+    // for this batch signature, else an eighth of the GPU (solves of a batch are short chains
+    // of latency-bound launches: spread over every SM, the cooperative and tensor-core
+    // kernels of one solve would leave no room for the others in flight)
+    bks_opts ob;
+    if (opts) ob = *opts; else bks_opts_default(&ob);
+    if (ob.max_sms <= 0) {
+        const auto it = ctx->batch_sms.find(batch_signature(batch, As, k, q, krylov, triplets));
+        ob.max_sms = it != ctx->batch_sms.end() ? it->second : default_batch_sms(ctx->num_sms);
+    }
     cudaEvent_t start = batch_begin(ctx, S);
     bks_status worst = BKS_OK;
     auto note = [&](int i, bks_status st_i, const bks_stats& one) {
@@ -1144,7 +1176,7 @@ bks_status batched_solve(bks_ctx* ctx, int batch, const bks_matrix* As, int k, i
             owner[h] = -1;
             const bks_status st_i = solve_entry(sub, &As[i], k, q, seeds ? seeds[i] : uint64_t(i),
                                                 pis ? pis[i] : nullptr, Zs[i], sigmas[i], Vs ? Vs[i] : nullptr,
-                                                opts, nullptr, krylov, triplets, true);
+                                                &ob, nullptr, krylov, triplets, true);
             if (sub->pending.active) owner[h] = i;
             else st_all[i] = st_i;
         }
@@ -1389,6 +1421,60 @@ bks_status bks_block_krylov_batched(bks_ctx* ctx, int batch, const bks_matrix* A
                                     bks_stats* stats, bks_status* statuses) {
     return batched_solve(ctx, batch, As, k, q, seeds, pis, Zs, sigmas, Vs, opts, stats, statuses, true, false,
                          "bks_block_krylov_batched");
+}
+
+bks_status bks_batched_autotune(bks_ctx* ctx, int batch, const bks_matrix* As, int k, int q,
+                                const uint64_t* seeds, const void* const* pis, void* const* Zs, void* const* sigmas,
+                                void* const* Vs, const bks_opts* opts, int* best_max_sms, float* best_ms) {
+    if (ctx == nullptr) return BKS_ERR_INVALID_ARG;
+    if (batch < 1) return fail(ctx, BKS_ERR_INVALID_ARG, "bks_batched_autotune needs a non-empty batch");
+    bks_opts ob;
+    if (opts) ob = *opts; else bks_opts_default(&ob);
+    DeviceGuard g(ctx->device);
+    const int n_sm = ctx->num_sms;
+    const int cands[] = {n_sm / 16, n_sm / 8, n_sm / 4, n_sm / 2, n_sm};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 0;
+    float best_t = 0.f;
+    bks_status worst = BKS_OK;
+    for (int trial = 0; trial < 2; ++trial)   // a warm-up pass over the candidates, then the timed one
+        for (int c : cands) {
+            if (c < 1) continue;
+            ob.max_sms = c;
+            cudaEventRecord(e0, ctx->stream);
+            const bks_status st = batched_solve(ctx, batch, As, k, q, seeds, pis, Zs, sigmas, Vs, &ob, nullptr,
+                                                nullptr, true, false, "bks_batched_autotune");
+            cudaEventRecord(e1, ctx->stream);
+            if (st != BKS_OK && st != BKS_WARN_DEFLATED) {
+                worst = st;
+                break;
+            }
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (trial == 1 && (best == 0 || ms < best_t)) {
+                best = c;
+                best_t = ms;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (worst != BKS_OK) return worst;
+    ctx->batch_sms[batch_signature(batch, As, k, q, true, false)] = best;
+    ob.max_sms = best;   // the outputs: those of the chosen budget
+    const bks_status st = batched_solve(ctx, batch, As, k, q, seeds, pis, Zs, sigmas, Vs, &ob, nullptr, nullptr,
+                                        true, false, "bks_batched_autotune");
+    if (best_max_sms) *best_max_sms = best;
+    if (best_ms) *best_ms = best_t;
+    return st;
+}
+
+int bks_batch_budget(const bks_ctx* ctx, int batch, const bks_matrix* As, int k, int q, int method) {
+    if (ctx == nullptr || batch < 1 || As == nullptr) return 0;
+    const auto it = ctx->batch_sms.find(batch_signature(batch, As, k, q, method == 0, false));
+    return it != ctx->batch_sms.end() ? it->second : default_batch_sms(ctx->num_sms);
 }
 
 bks_status bks_ritz_triplets_batched(bks_ctx* ctx, int batch, const bks_matrix* As, int k, int q,

@@ -143,8 +143,8 @@ def test_recompute_mode_keeps_no_triplets():
 def test_batched_forward_backward_matches_oracle_and_single(recompute):
     """Uneven shapes whose Krylov width covers min(n, d) (k = 16, q = 4: width 48, 64 or 80
     after the cap), where the gradient is exact: every matrix's gradient matches the FP64
-    oracle's loss gradient, and the batched forward + backward equal the single calls bit
-    for bit."""
+    oracle's loss gradient, and the batched forward + backward equal the single calls (made
+    with the batch's SM budget) bit for bit."""
     shapes = [(64, 48), (120, 64), (80, 200), (96, 80), (48, 300), (256, 64)]
     k, q = 16, 4
     mats, targets = [], []
@@ -161,7 +161,7 @@ def test_batched_forward_backward_matches_oracle_and_single(recompute):
         g_ora = grad.loss_grad(a, k, t)
         assert rel(ats[i].grad.cpu().numpy(), g_ora) < 1e-7, i
         single = cuda(a, torch.float64).requires_grad_(True)
-        sk, ak = bk.rand_svd(single, k, q, pi=pis[i])
+        sk, ak = bk.rand_svd(single, k, q, pi=pis[i], max_sms=bk.batch_budget(ats, k, q))
         loss_of(sk, ak, cuda(t, torch.float64)).backward()
         assert torch.equal(single.grad, ats[i].grad), i
         assert torch.equal(sk, outs[i][0]) and torch.equal(ak, outs[i][1]), i
@@ -178,7 +178,7 @@ def test_batched_uneven_workload_equals_single():
     sum(loss_of(sk, ak, cuda(t, torch.float32)) for (sk, ak), t in zip(outs, ts)).backward()
     for i, (a, t) in enumerate(zip(mats, ts)):
         single = cuda(a, torch.float32).requires_grad_(True)
-        sk, ak = bk.rand_svd(single, k, q, seed=i)
+        sk, ak = bk.rand_svd(single, k, q, seed=i, max_sms=bk.batch_budget(ats, k, q))
         loss_of(sk, ak, cuda(t, torch.float32)).backward()
         assert torch.equal(single.grad, ats[i].grad), i
 

@@ -92,8 +92,9 @@ def test_block_p_batched_equals_single_solves():
     mats = synth.batched_planted(batch=6, k=8, seed=44, m_range=(200, 400), n_range=(150, 300))
     ams = [dev(m) for m in mats]
     outs = bk.block_krylov_batched(ams, 8, 2, seeds=list(range(6)), block_p=12)
+    sms = bk.batch_budget(ams, 8, 2)
     for i, (z, s) in enumerate(outs):
-        z1, s1 = bk.block_krylov(ams[i], 8, 2, seed=i, block_p=12)
+        z1, s1 = bk.block_krylov(ams[i], 8, 2, seed=i, block_p=12, max_sms=sms)
         assert torch.equal(z, z1) and torch.equal(s, s1)
 
 
