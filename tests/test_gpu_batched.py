@@ -89,3 +89,24 @@ def test_autotune_caches_a_budget_and_batches_reuse_it():
     explicit = bk.block_krylov_batched(ams, k, q, seeds=list(range(24)), max_sms=n_sm)
     z1, s1 = bk.block_krylov(ams[5], k, q, seed=5)
     assert torch.equal(explicit[5][0], z1) and torch.equal(explicit[5][1], s1)
+
+
+def test_batch_at_the_full_shape_ranges():
+    """32 matrices drawn from the batched workload's full ranges (m in [256, 4096], n in
+    [128, 2048], sigma_i = 1/i plus 1e-3 noise, k = 16, q = 4): every member equals its single
+    call at the batch's SM budget bit for bit, and a sample of three matches the FP64 oracle
+    (relative 1e-5 on the Ritz values)."""
+    mats = synth.batched_planted(batch=32, k=16, seed=1005)
+    k, q = 16, 4
+    ams = [dev(a) for a in mats]
+    pis = [dev(synth.gaussian_pi(300 + i, a.shape[1], k)) for i, a in enumerate(mats)]
+    outs, _, statuses = bk.block_krylov_batched(ams, k, q, pis=pis, stats=True)
+    assert all(s in (0, 100) for s in statuses)
+    sms = bk.batch_budget(ams, k, q)
+    for i in range(32):
+        z1, s1 = bk.block_krylov(ams[i], k, q, pi=pis[i], max_sms=sms)
+        assert torch.equal(outs[i][0], z1) and torch.equal(outs[i][1], s1), i
+    for i in (0, 13, 31):
+        ref = krylov.block_krylov(mats[i].astype(np.float64), k, q, pis[i].cpu().numpy())
+        sg = outs[i][1].double().cpu().numpy()
+        assert np.max(np.abs(sg - ref.sigma) / ref.sigma) <= 1e-5, i
