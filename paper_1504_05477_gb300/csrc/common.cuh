@@ -239,6 +239,9 @@ bool topk_values(Exec& ex, int w, const T* M, int m, T* scratch, const T** lam, 
 // matching rows of Ut, k x ldu).
 template <typename T>
 void sign_fix(Exec& ex, T* Z, int64_t n, int k, int64_t ldz, T* Ut, int64_t w, int64_t ldu);
+// The same on a column-major Zt (column i at Zt + i ldz): coalesced column scans.
+template <typename T>
+void sign_fix_cm(Exec& ex, T* Zt, int64_t n, int k, int64_t ldz, T* Ut, int64_t w, int64_t ldu);
 
 // sigma_i = |row i of Vt| (FP64 accumulation); optionally scale row i by 1/sigma_i.
 template <typename T>

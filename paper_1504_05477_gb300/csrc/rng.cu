@@ -76,12 +76,12 @@ __global__ void check_finite_kernel(const T* __restrict__ x, int64_t n, int* sta
 // One CTA per column: find the entry of largest magnitude (lowest row on ties) and
 // flip the column (and row c of Ut) if it is negative.
 template <typename T>
-__global__ void sign_fix_kernel(T* Z, int64_t n, int64_t ldz, T* Ut, int64_t w, int64_t ldu) {
+__global__ void sign_fix_kernel(T* Z, int64_t n, int64_t rs, int64_t cs, T* Ut, int64_t w, int64_t ldu) {
     const int c = blockIdx.x;
     T best = T(-1);
     int64_t bidx = INT64_MAX;
     for (int64_t r = threadIdx.x; r < n; r += blockDim.x) {
-        const T v = fabs(Z[r * ldz + c]);
+        const T v = fabs(Z[r * rs + c * cs]);
         if (v > best) { best = v; bidx = r; }
     }
     __shared__ T sb[1024];
@@ -103,8 +103,8 @@ __global__ void sign_fix_kernel(T* Z, int64_t n, int64_t ldz, T* Ut, int64_t w, 
     const int64_t imax = si[0];
     __syncthreads();
     if (imax == INT64_MAX) return;
-    if (!(Z[imax * ldz + c] < T(0))) return;
-    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) Z[r * ldz + c] = -Z[r * ldz + c];
+    if (!(Z[imax * rs + c * cs] < T(0))) return;
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) Z[r * rs + c * cs] = -Z[r * rs + c * cs];
     if (Ut != nullptr)
         for (int64_t j = threadIdx.x; j < w; j += blockDim.x) Ut[c * ldu + j] = -Ut[c * ldu + j];
 }
@@ -213,7 +213,13 @@ void check_finite(Exec& ex, const T* x, int64_t n) {
 
 template <typename T>
 void sign_fix(Exec& ex, T* Z, int64_t n, int k, int64_t ldz, T* Ut, int64_t w, int64_t ldu) {
-    sign_fix_kernel<T><<<k, 1024, 0, ex.stream>>>(Z, n, ldz, Ut, w, ldu);
+    sign_fix_kernel<T><<<k, 1024, 0, ex.stream>>>(Z, n, ldz, 1, Ut, w, ldu);
+    ex.launches++;
+}
+
+template <typename T>
+void sign_fix_cm(Exec& ex, T* Zt, int64_t n, int k, int64_t ldz, T* Ut, int64_t w, int64_t ldu) {
+    sign_fix_kernel<T><<<k, 1024, 0, ex.stream>>>(Zt, n, 1, ldz, Ut, w, ldu);
     ex.launches++;
 }
 
@@ -229,6 +235,7 @@ void row_norms(Exec& ex, T* Vt, int k, int64_t len, int64_t ldv, T* sigma, bool 
                                   int64_t);                                                \
     template void check_finite<T>(Exec&, const T*, int64_t);                               \
     template void sign_fix<T>(Exec&, T*, int64_t, int, int64_t, T*, int64_t, int64_t);     \
+    template void sign_fix_cm<T>(Exec&, T*, int64_t, int, int64_t, T*, int64_t, int64_t);  \
     template void row_norms<T>(Exec&, T*, int, int64_t, int64_t, T*, bool);
 BKS_INST(float)
 BKS_INST(double)

@@ -904,7 +904,11 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
                               cudaMemcpyDeviceToDevice, ex.stream);
             tc_ritz = tc_product_f32(ex, reinterpret_cast<const float*>(Qt), wr, n, p.ldn, true, kout, vtp, p.ldvt,
                                      zt, p.ldn, pw.xh, pw.xl, pw.tpart, pw.tpart_cap);
-            if (tc_ritz) transpose_in<T>(ex, zt, BKS_F32, kout, n, p.ldn, Z, kout);
+            if (tc_ritz) {
+                // the sign fix scans the column-major Z^T (contiguous columns), then Z is transposed
+                if (o.sign_fix) sign_fix_cm<T>(ex, reinterpret_cast<T*>(zt), n, kout, p.ldn, Vt, wr, wr);
+                transpose_in<T>(ex, zt, BKS_F32, kout, n, p.ldn, Z, kout);
+            }
         }
         if (!tc_ritz) {
             GemmDesc gz{};
@@ -914,7 +918,7 @@ bks_status solve(bks_ctx* ctx, const bks_matrix* A, int kz, int q, uint64_t seed
             gz.out = Z; gz.ldo = kout; gz.out_transposed = true; gz.alpha = 1.0; gz.beta = 0.0;
             gemm_simt<T>(ex, gz, part, p.part_cap);
         }
-        if (o.sign_fix) sign_fix<T>(ex, Z, n, kout, kout, Vt, wr, wr);
+        if (o.sign_fix && !tc_ritz) sign_fix<T>(ex, Z, n, kout, kout, Vt, wr, wr);
         // sigma_i = |B ubar_i| = |A^T z_i|; V_k = B Ubar_k Sigma^{-1} (same two routes, after
         // the sign fix has flipped the rows of Vt)
         bool tc_v = false;
