@@ -27,6 +27,8 @@ namespace {
 
 constexpr int TD_NT = 512;                   // threads per CTA of the reduction
 constexpr int TD_NW = TD_NT / 32;
+constexpr int TD_ROWS = 2;                   // rows of a gathered column per thread (w <= 1024)
+constexpr int TD_PART = 8;                   // partial sums of p . v per lane (C TD_NW <= 256)
 constexpr size_t SMEM_MAX = 200 * 1024;      // shared bytes per CTA the kernels may use
 constexpr int WY_NB = 16;                    // reflectors per compact-WY block
 constexpr int WY_WARPS = 4;                  // vectors per CTA of the back-transformation
@@ -62,7 +64,8 @@ TdShape td_shape(int w, int C) {
     s.tpc = TD_NT / p2 < 32 ? TD_NT / p2 : 32;
     s.wp = round_up(w, 32) + (s.tpc < 32 ? s.tpc : 0);
     const size_t nlp = size_t(round_up(s.nl, 4));
-    s.smem = (size_t(s.nl + 5) * s.wp + 2 * nlp + 3 * TD_NW + 4) * sizeof(T);
+    s.smem = (size_t(s.nl + 3) * s.wp + 2 * nlp + 3 * TD_NW + 4) * sizeof(T);
+    if (w > TD_ROWS * TD_NT || C * TD_NW > 32 * TD_PART) return TdShape{};
     return s;
 }
 
@@ -84,13 +87,14 @@ TdShape td_pick(int w) {
 // 1 / max_i M_ii.  CTA r keeps columns c = l C + r (l < nl).  Step j: every CTA holds
 // column j (rows j..w-1) in xa and derives the same reflector H_j = I - tau v v^T from it
 // (v[j+1] = 1, v_i = s x_i below; all CTAs compute it in the same order, so bit for bit);
-// tpc threads per own column c > j form p_c = tau A(j+1:, c) . v; the owner of column
-// j+1 publishes it.  After the cluster barrier each CTA gathers p, K = (tau / 2) p . v,
-// w = p - K v, updates its columns, A -= v w^T + w v^T, and the published column, which
-// becomes the next step's xa (double-buffered).  Per step: one cluster barrier and two
-// CTA barriers.  Outputs: dT (w), eT (w - 1), tau (w - 1), max_i M_ii in tau[w - 1] (the
-// eigenvalues of M are those of T times it) and the reflectors: row j of V holds v_j in
-// columns j+1..w-1.
+// tpc threads per own column c > j form p_c = tau A(j+1:, c) . v.  After the cluster
+// barrier each CTA gathers p, K = (tau / 2) p . v and column j+1 (read in place from its
+// owner: no step after j-1 writes it; all these remote loads are issued before any of
+// them is used), forms w = p - K v, updates its columns, A -= v w^T + w v^T, and column
+// j+1, which becomes the next step's xa (double-buffered).  Per step: one cluster barrier
+// and two CTA barriers.  Outputs: dT (w), eT (w - 1), tau (w - 1), max_i M_ii in
+// tau[w - 1] (the eigenvalues of M are those of T times it) and the reflectors: row j of
+// V holds v_j in columns j+1..w-1.
 template <typename T>
 __global__ void __launch_bounds__(TD_NT) tridiag_kernel(const T* __restrict__ M, int w, int tpc, int64_t wp,
                                                         T* __restrict__ dT, T* __restrict__ eT,
@@ -105,8 +109,7 @@ __global__ void __launch_bounds__(TD_NT) tridiag_kernel(const T* __restrict__ M,
     T* A = reinterpret_cast<T*>(td_smem_raw);   // nl x wp
     T* xv = A + size_t(nl) * wp;                // 2 x wp: current column, next column
     T* pv = xv + 2 * wp;                        // gathered p (raw)
-    T* cbuf = pv + wp;                          // 2 x wp: published column
-    T* pbuf = cbuf + 2 * wp;                    // 2 x nlp: p of the own columns
+    T* pbuf = pv + wp;                          // 2 x nlp: p of the own columns
     T* red2 = pbuf + 2 * nlp;                   // 2 x TD_NW: warp partials of p . v
     T* red = red2 + 2 * TD_NW;                  // TD_NW: warp partials of |x|^2
     T* misc = red + TD_NW;                      // [K]
@@ -195,30 +198,42 @@ __global__ void __launch_bounds__(TD_NT) tridiag_kernel(const T* __restrict__ M,
             dp = warp_sum(dp);
             if (lane == 0) red2[par * TD_NW + warp] = dp;
         }
+        // column j+1 of the owner's A: written last by step j-1, read-only from here on
         const int own1 = (j + 1) & (C - 1);
-        if (r == own1) {
-            const T* col = A + ((j + 1) >> lc) * wp;
-            for (int i = j + 1 + tid; i < w; i += TD_NT) cbuf[par * wp + i] = col[i];
-        }
         cl.sync();
-        const T* ycol = cl.map_shared_rank(cbuf + par * wp, own1);
+        const T* ycol = cl.map_shared_rank(A + ((j + 1) >> lc) * wp, own1);
+        T yr[TD_ROWS];
+#pragma unroll
+        for (int u = 0; u < TD_ROWS; ++u) {
+            const int i = j + 1 + tid + u * TD_NT;
+            yr[u] = i < w ? ycol[i] : T(0);
+        }
         T ssn = T(0);
         if (act) {
             for (int i = j + 1 + tid; i < w; i += TD_NT)
                 pv[i] = cl.map_shared_rank(pbuf + par * nlp, i & (C - 1))[i >> lc];
             if (warp == 0) {
+                T part[TD_PART];
+#pragma unroll
+                for (int u = 0; u < TD_PART; ++u) {
+                    const int q = lane + 32 * u;
+                    part[u] = q < C * TD_NW ? cl.map_shared_rank(red2 + par * TD_NW, q / TD_NW)[q % TD_NW] : T(0);
+                }
                 T dsum = T(0);
-                for (int q = lane; q < C * TD_NW; q += 32)
-                    dsum += cl.map_shared_rank(red2 + par * TD_NW, q / TD_NW)[q % TD_NW];
+#pragma unroll
+                for (int u = 0; u < TD_PART; ++u) dsum += part[u];
                 dsum = warp_sum(dsum);
                 if (lane == 0) misc[0] = T(0.5) * tau * dsum;
             }
             __syncthreads();   // pv, K
             const T K = misc[0];
             const T w1 = pv[j + 1] - K;   // v[j+1] = 1
-            for (int i = j + 1 + tid; i < w; i += TD_NT) {
+#pragma unroll
+            for (int u = 0; u < TD_ROWS; ++u) {
+                const int i = j + 1 + tid + u * TD_NT;
+                if (i >= w) break;
                 const T vi = i == j + 1 ? T(1) : xa[i] * scal;
-                const T x = ycol[i] - (vi * w1 + (pv[i] - K * vi));
+                const T x = yr[u] - (vi * w1 + (pv[i] - K * vi));
                 xb[i] = x;
                 if (i >= j + 3) ssn += x * x;
             }
@@ -231,8 +246,11 @@ __global__ void __launch_bounds__(TD_NT) tridiag_kernel(const T* __restrict__ M,
                 }
             }
         } else {
-            for (int i = j + 1 + tid; i < w; i += TD_NT) {
-                const T x = ycol[i];
+#pragma unroll
+            for (int u = 0; u < TD_ROWS; ++u) {
+                const int i = j + 1 + tid + u * TD_NT;
+                if (i >= w) break;
+                const T x = yr[u];
                 xb[i] = x;
                 if (i >= j + 3) ssn += x * x;
             }
