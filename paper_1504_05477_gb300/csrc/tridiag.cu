@@ -19,6 +19,7 @@
 #include <cfloat>
 
 #include "common.cuh"
+#include "tc_common.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -32,6 +33,12 @@ constexpr int TD_PART = 8;                   // partial sums of p . v per lane (
 constexpr size_t SMEM_MAX = 200 * 1024;      // shared bytes per CTA the kernels may use
 constexpr int WY_NB = 16;                    // reflectors per compact-WY block
 constexpr int WY_WARPS = 4;                  // vectors per CTA of the back-transformation
+constexpr int WY_MAXS = 4;                   // ring slots of reflector blocks (back-transformation)
+
+// Row pitch of the reflector matrix V: a multiple of 16 bytes, so that a block of WY_NB
+// rows is one contiguous bulk copy.  V has round_up(w, WY_NB) rows, zero outside the
+// reflectors' supports.
+__host__ __device__ constexpr int64_t v_pitch(int w) { return (int64_t(w) + 3) / 4 * 4; }
 
 template <typename T> __device__ __forceinline__ T fast_div(T a, T b) { return a / b; }
 template <> __device__ __forceinline__ float fast_div<float>(float a, float b) { return __fdividef(a, b); }
@@ -94,7 +101,7 @@ TdShape td_pick(int w) {
 // j+1, which becomes the next step's xa (double-buffered).  Per step: one cluster barrier
 // and two CTA barriers.  Outputs: dT (w), eT (w - 1), tau (w - 1), max_i M_ii in
 // tau[w - 1] (the eigenvalues of M are those of T times it) and the reflectors: row j of
-// V holds v_j in columns j+1..w-1.
+// V (pitch v_pitch(w)) holds v_j in columns j+1..w-1.
 template <typename T>
 __global__ void __launch_bounds__(TD_NT) tridiag_kernel(const T* __restrict__ M, int w, int tpc, int64_t wp,
                                                         T* __restrict__ dT, T* __restrict__ eT,
@@ -173,7 +180,7 @@ __global__ void __launch_bounds__(TD_NT) tridiag_kernel(const T* __restrict__ M,
                 tau_out[j] = tau;
             }
             for (int i = j + 1 + tid; i < w; i += TD_NT)
-                V[int64_t(j) * w + i] = act ? (i == j + 1 ? T(1) : xa[i] * scal) : T(0);
+                V[int64_t(j) * v_pitch(w) + i] = act ? (i == j + 1 ? T(1) : xa[i] * scal) : T(0);
         }
         if (act) {
             // p_c = tau (A(j+1, c) + scal sum_{i >= j+2} A(i, c) x_i)
@@ -350,14 +357,16 @@ __device__ __forceinline__ float start_entry(int i, int t) {
 }
 
 // Inverse iteration, one thread per eigenvalue, vpc per CTA, everything in shared memory
-// ([i][vector] layout).  Each of the two rounds eliminates T - lam_t I with partial
-// pivoting while applying the same steps to the right-hand side (the pseudo-random start,
-// then the previous round's normalised solution), keeping U (reciprocal pivot and two
-// super-diagonals) for the back substitution.  Tiny pivots are raised to eps |T|.
+// ([i][vector] layout).  The first round eliminates T - lam_t I with partial pivoting
+// while applying the same steps to the right-hand side (a pseudo-random start), keeping
+// U (reciprocal pivot and two super-diagonals) for the back substitution and each
+// step's row swap and multiplier; the second round applies only those stored steps to
+// its right-hand side (the first round's normalised solution) and substitutes back
+// through the same U.  Tiny pivots are raised to eps |T|.
 // Output: X (m x ldx, row t = unit vector t, zero pad).
 template <typename T>
 size_t invit_smem(int w, int vpc) {
-    return (size_t(2) * w + size_t(4) * w * vpc) * sizeof(T);
+    return (size_t(2) * w + size_t(6) * w * vpc) * sizeof(T);
 }
 
 template <typename T>
@@ -373,6 +382,8 @@ __global__ void invit_kernel(const T* __restrict__ dT, const T* __restrict__ eT,
     T* U1 = R0 + size_t(w) * vpc;
     T* U2 = U1 + size_t(w) * vpc;
     T* Z = U2 + size_t(w) * vpc;        // right-hand side, then solution
+    T* MU = Z + size_t(w) * vpc;        // multipliers of the elimination
+    T* SW = MU + size_t(w) * vpc;       // 1: rows i and i+1 swapped at step i
     for (int i = threadIdx.x; i < w; i += vpc) {
         d[i] = dT[i];
         e[i] = i + 1 < w ? eT[i] : T(0);
@@ -388,40 +399,54 @@ __global__ void invit_kernel(const T* __restrict__ dT, const T* __restrict__ eT,
         const T lt = lam[t];
         for (int round = 0; round < 2; ++round) {
             const T sprev = scale;
-            auto rhs = [&](int i) -> T {
-                return round == 0 ? T(start_entry(i, t)) : Z[size_t(i) * vpc + tl] * sprev;
-            };
             T r0 = d[0] - lt, r1 = e[0];
-            T ry = rhs(0);
-            for (int i = 0; i + 1 < w; ++i) {
-                const T ei = e[i];
-                const T an = d[i + 1] - lt;
-                const T en = e[i + 1];
-                const T yn = rhs(i + 1);
-                const size_t o = size_t(i) * vpc + tl;
-                // pivot row: the active row (no swap) or row i+1 (swap), whichever has
-                // the larger entry in column i
-                const bool sw = fabs(ei) > fabs(r0);
-                if (!sw && fabs(r0) < pert) r0 = copysign(pert, r0);
-                const T piv = sw ? ei : r0;
-                const T oth = sw ? r0 : ei;
-                const T rc = recip(piv);
-                const T mu = oth * rc;
-                R0[o] = rc;
-                U1[o] = sw ? an : r1;
-                U2[o] = sw ? en : T(0);
-                Z[o] = sw ? yn : ry;
-                const T ry_n = sw ? ry - mu * yn : yn - mu * ry;
-                const T r0_n = sw ? r1 - mu * an : an - mu * r1;
-                r1 = sw ? -mu * en : en;
-                ry = ry_n;
-                r0 = r0_n;
+            T ry = round == 0 ? T(start_entry(0, t)) : Z[tl] * sprev;
+            if (round == 0) {
+                for (int i = 0; i + 1 < w; ++i) {
+                    const T ei = e[i];
+                    const T an = d[i + 1] - lt;
+                    const T en = e[i + 1];
+                    const T yn = T(start_entry(i + 1, t));
+                    const size_t o = size_t(i) * vpc + tl;
+                    // pivot row: the active row (no swap) or row i+1 (swap), whichever has
+                    // the larger entry in column i
+                    const bool sw = fabs(ei) > fabs(r0);
+                    if (!sw && fabs(r0) < pert) r0 = copysign(pert, r0);
+                    const T piv = sw ? ei : r0;
+                    const T oth = sw ? r0 : ei;
+                    const T rc = recip(piv);
+                    const T mu = oth * rc;
+                    R0[o] = rc;
+                    U1[o] = sw ? an : r1;
+                    U2[o] = sw ? en : T(0);
+                    MU[o] = mu;
+                    SW[o] = sw ? T(1) : T(0);
+                    Z[o] = sw ? yn : ry;
+                    const T ry_n = sw ? ry - mu * yn : yn - mu * ry;
+                    const T r0_n = sw ? r1 - mu * an : an - mu * r1;
+                    r1 = sw ? -mu * en : en;
+                    ry = ry_n;
+                    r0 = r0_n;
+                }
+            } else {
+                // the stored row operations on the new right-hand side (row i+1 is read
+                // before step i+1 overwrites it)
+                for (int i = 0; i + 1 < w; ++i) {
+                    const size_t o = size_t(i) * vpc + tl;
+                    const T yn = Z[o + vpc] * sprev;
+                    const bool sw = SW[o] != T(0);
+                    const T mu = MU[o];
+                    Z[o] = sw ? yn : ry;
+                    ry = sw ? ry - mu * yn : yn - mu * ry;
+                }
             }
-            if (fabs(r0) < pert) r0 = copysign(pert, r0);
             const size_t ol = size_t(w - 1) * vpc + tl;
-            R0[ol] = recip(r0);
-            U1[ol] = T(0);
-            U2[ol] = T(0);
+            if (round == 0) {
+                if (fabs(r0) < pert) r0 = copysign(pert, r0);
+                R0[ol] = recip(r0);
+                U1[ol] = T(0);
+                U2[ol] = T(0);
+            }
             Z[ol] = ry;
             // back substitution; when the solution grows past BIG (many pivots at the
             // eps |T| floor, as for eigenvalues of a numerical null space), the whole
@@ -472,7 +497,7 @@ __device__ void stage_block(const T* __restrict__ V, int w, int q0, int nb, T* V
     for (int i = threadIdx.x; i < w; i += blockDim.x) {
         T r[WY_NB];
 #pragma unroll
-        for (int a = 0; a < WY_NB; ++a) r[a] = (a < nb && i > q0 + a) ? V[int64_t(q0 + a) * w + i] : T(0);
+        for (int a = 0; a < WY_NB; ++a) r[a] = (a < nb && i > q0 + a) ? V[int64_t(q0 + a) * v_pitch(w) + i] : T(0);
 #pragma unroll
         for (int a = 0; a < WY_NB; ++a) Vs[a * wp + i] = r[a];
     }
@@ -521,75 +546,124 @@ __global__ void wy_factor_kernel(const T* __restrict__ V, const T* __restrict__ 
 }
 
 // Vt row t = H_0 ... H_{nref-1} x_t, the blocks applied last to first as
-// x -= Vb (Tb (Vb^T x)); one warp per vector.
+// x -= Vb (Tb (Vb^T x)); one warp per vector.  The reflector blocks (WY_NB rows of V,
+// zero outside their supports, and their Tb) stream through a ring of ns slots in
+// shared memory, each filled by two bulk copies that complete on the slot's mbarrier,
+// so the next blocks' loads overlap the current block's arithmetic.  Every wait is
+// bounded (ST_TIMEOUT).
 template <typename T>
 __global__ void __launch_bounds__(WY_WARPS * 32) wy_apply_kernel(const T* __restrict__ X, int64_t ldx, int w,
                                                                  int m, int nref, const T* __restrict__ V,
                                                                  const T* __restrict__ Tw, T* __restrict__ Vt,
-                                                                 int64_t ldv) {
-    extern __shared__ __align__(16) unsigned char wy_smem[];
-    const int64_t wp = (int64_t(w) + 3) / 4 * 4;
-    T* xs = reinterpret_cast<T*>(wy_smem);      // WY_WARPS x wp
-    T* Vs = xs + WY_WARPS * wp;                 // NB x wp
-    __shared__ T Ts[WY_NB * WY_NB];
+                                                                 int64_t ldv, int ns, int* __restrict__ status) {
+    extern __shared__ __align__(128) unsigned char wy_smem[];
+    __shared__ uint64_t full[WY_MAXS];
+    __shared__ int abort_flag;
+    const int64_t vp = v_pitch(w);
+    const int64_t slot = WY_NB * vp + WY_NB * WY_NB;          // elements per ring slot
+    const uint32_t vbytes = uint32_t(WY_NB * vp * sizeof(T)), tbytes = uint32_t(WY_NB * WY_NB * sizeof(T));
+    T* ring = reinterpret_cast<T*>(wy_smem);
+    T* xs = ring + ns * slot;                                 // WY_WARPS x vp
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int t = blockIdx.x * WY_WARPS + warp;
-    T* x = xs + warp * wp;
+    const int nblk = (nref + WY_NB - 1) / WY_NB;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < ns; ++q) tc::mbar_init(&full[q], 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // use u = 0, 1, ... takes block b = nblk - 1 - u in slot u % ns
+    auto issue = [&](int u) {
+        const int b = nblk - 1 - u;
+        T* dst = ring + (u % ns) * slot;
+        uint64_t* bar = &full[u % ns];
+        tc::mbar_expect_tx(bar, vbytes + tbytes);
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         tc::smem_u32(dst)),
+                     "l"(V + int64_t(b) * WY_NB * vp), "r"(vbytes), "r"(tc::smem_u32(bar))
+                     : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         tc::smem_u32(dst + WY_NB * vp)),
+                     "l"(Tw + int64_t(b) * WY_NB * WY_NB), "r"(tbytes), "r"(tc::smem_u32(bar))
+                     : "memory");
+    };
+    if (threadIdx.x == 0)
+        for (int u = 0; u < ns && u < nblk; ++u) issue(u);
+    T* x = xs + warp * vp;
     if (t < m)
         for (int i = lane; i < w; i += 32) x[i] = X[int64_t(t) * ldx + i];
-    const int nblk = (nref + WY_NB - 1) / WY_NB;
-    for (int b = nblk - 1; b >= 0; --b) {
-        const int q0 = b * WY_NB;
-        const int nb = nref - q0 < WY_NB ? nref - q0 : WY_NB;
-        __syncthreads();
-        stage_block(V, w, q0, nb, Vs, wp);
-        for (int p = threadIdx.x; p < WY_NB * WY_NB; p += blockDim.x) Ts[p] = Tw[int64_t(b) * WY_NB * WY_NB + p];
-        __syncthreads();
-        if (t >= m) continue;
-        T acc[WY_NB];
+    int issued = ns < nblk ? ns : nblk;
+    for (int u = 0; u < nblk; ++u) {
+        const int b = nblk - 1 - u, q0 = b * WY_NB;
+        const T* Vs = ring + (u % ns) * slot;
+        const T* Ts = Vs + WY_NB * vp;
+        const bool ok = tc::wait_bar(&full[u % ns], uint32_t((u / ns) & 1), &abort_flag, status);
+        if (ok && t < m) {
+            T acc[WY_NB];
 #pragma unroll
-        for (int a = 0; a < WY_NB; ++a) acc[a] = T(0);
-        for (int i = q0 + 1 + lane; i < w; i += 32) {
-            const T xi = x[i];
+            for (int a = 0; a < WY_NB; ++a) acc[a] = T(0);
+            for (int i = q0 + 1 + lane; i < w; i += 32) {
+                const T xi = x[i];
 #pragma unroll
-            for (int a = 0; a < WY_NB; ++a) acc[a] += Vs[a * wp + i] * xi;
+                for (int a = 0; a < WY_NB; ++a) acc[a] += Vs[a * vp + i] * xi;
+            }
+#pragma unroll
+            for (int a = 0; a < WY_NB; ++a) acc[a] = warp_sum(acc[a]);
+            T mt = T(0);   // lane a < NB: (Tb s)_a
+#pragma unroll
+            for (int c = 0; c < WY_NB; ++c) mt += (lane < WY_NB ? Ts[lane * WY_NB + c] : T(0)) * acc[c];
+            T tv[WY_NB];
+#pragma unroll
+            for (int a = 0; a < WY_NB; ++a) tv[a] = __shfl_sync(0xffffffffu, mt, a);
+            for (int i = q0 + 1 + lane; i < w; i += 32) {
+                T sm = T(0);
+#pragma unroll
+                for (int a = 0; a < WY_NB; ++a) sm += Vs[a * vp + i] * tv[a];
+                x[i] -= sm;
+            }
         }
-#pragma unroll
-        for (int a = 0; a < WY_NB; ++a) acc[a] = warp_sum(acc[a]);
-        T mt = T(0);   // lane a < NB: (Tb s)_a
-#pragma unroll
-        for (int c = 0; c < WY_NB; ++c) mt += (lane < WY_NB ? Ts[lane * WY_NB + c] : T(0)) * acc[c];
-        T tv[WY_NB];
-#pragma unroll
-        for (int a = 0; a < WY_NB; ++a) tv[a] = __shfl_sync(0xffffffffu, mt, a);
-        for (int i = q0 + 1 + lane; i < w; i += 32) {
-            T s = T(0);
-#pragma unroll
-            for (int a = 0; a < WY_NB; ++a) s += Vs[a * wp + i] * tv[a];
-            x[i] -= s;
+        __syncthreads();   // slot u % ns is free
+        if (threadIdx.x == 0 && issued < nblk && !abort_flag) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(issued);
+            ++issued;
         }
-        __syncwarp();
     }
-    if (t < m)
+    // every copy issued has landed before shared memory is released (bounded)
+    if (threadIdx.x == 0)
+        for (int u = issued > ns ? issued - ns : 0; u < issued; ++u) tc::drain_bar(&full[u % ns], (u / ns) & 1);
+    __syncthreads();
+    if (t < m && !abort_flag)
         for (int i = lane; i < w; i += 32) Vt[int64_t(t) * ldv + i] = x[i];
+}
+
+// ring slots of the back-transformation that fit next to the vectors (0: too wide)
+template <typename T>
+int wy_slots(int w) {
+    const size_t vp = size_t(v_pitch(w));
+    const size_t slot = (WY_NB * vp + WY_NB * WY_NB) * sizeof(T), xb = WY_WARPS * vp * sizeof(T);
+    if (xb >= SMEM_MAX) return 0;
+    const size_t n = (SMEM_MAX - xb) / slot;
+    return n >= 2 ? int(n < WY_MAXS ? n : WY_MAXS) : 0;
 }
 
 template <typename T>
 size_t wy_apply_smem(int w) {
-    return size_t(WY_WARPS + WY_NB) * round_up(w, 4) * sizeof(T);
+    const size_t vp = size_t(v_pitch(w));
+    return (size_t(wy_slots<T>(w)) * (WY_NB * vp + WY_NB * WY_NB) + WY_WARPS * vp) * sizeof(T);
 }
 
 }  // namespace
 
 template <typename T>
 bool tridiag_fits(int w, int m) {
-    return w >= 3 && m >= 1 && m <= w && td_pick<T>(w).C > 0 && invit_vpc<T>(w) > 0 &&
-           wy_apply_smem<T>(w) <= SMEM_MAX;
+    return w >= 3 && m >= 1 && m <= w && td_pick<T>(w).C > 0 && invit_vpc<T>(w) > 0 && wy_slots<T>(w) > 0;
 }
 
 // Scratch layout (element offsets, each buffer starting on a 64-element boundary): dT,
-// eT, tau, |T| (w each), lam (m), V (w x w), X and its orthonormalisation scratch
-// (m x ldx each), WY factors (ceil(w / NB) NB^2).
+// eT, tau, |T| (w each), lam (m), V (round_up(w, NB) x v_pitch(w)), X and its
+// orthonormalisation scratch (m x ldx each), WY factors (ceil(w / NB) NB^2).
 struct TdScratch {
     size_t dT, eT, tau, tn, lam, V, X, Xtmp, Tw, total;
     TdScratch(int w, int m) {
@@ -598,7 +672,8 @@ struct TdScratch {
         size_t o = 0;
         auto take = [&](size_t n) { const size_t at = o; o += size_t(round_up(int64_t(n), 64)); return at; };
         dT = take(w); eT = take(w); tau = take(w); tn = take(w); lam = take(m);
-        V = take(size_t(w) * w); X = take(size_t(m) * ldx); Xtmp = take(size_t(m) * ldx);
+        V = take(size_t(round_up(w, WY_NB)) * size_t(v_pitch(w)));
+        X = take(size_t(m) * ldx); Xtmp = take(size_t(m) * ldx);
         Tw = take(nblk * WY_NB * WY_NB);
         total = o;
     }
@@ -669,6 +744,8 @@ bool topk_tridiag(Exec& ex, int w, const T* M, int m, T* Vt, int64_t ldv, T* scr
     T* X = scratch + L.X;
     T* Xtmp = scratch + L.Xtmp;
     T* Tw = scratch + L.Tw;
+    // the reduction writes each reflector's support only: the rest of V stays zero
+    cudaMemsetAsync(V, 0, size_t(round_up(w, WY_NB)) * size_t(v_pitch(w)) * sizeof(T), ex.stream);
     if (!reduce_and_bisect(ex, w, M, m, scratch, L)) return false;
     const int vpc = invit_vpc<T>(w);
     const size_t ismem = invit_smem<T>(w, vpc);
@@ -681,13 +758,13 @@ bool topk_tridiag(Exec& ex, int w, const T* M, int m, T* Vt, int64_t ldv, T* scr
     orth_block<T>(ex, w, ldx, X, 0, X, m, Xtmp, X, ows);
     const int nref = w - 2;
     const int nblk = (nref + WY_NB - 1) / WY_NB;
-    const size_t fsmem = size_t(WY_NB) * round_up(w, 4) * sizeof(T);
+    const size_t fsmem = size_t(WY_NB) * v_pitch(w) * sizeof(T);
     if (fsmem > 48 * 1024) allow_dynamic_smem(reinterpret_cast<const void*>(wy_factor_kernel<T>), fsmem);
     wy_factor_kernel<T><<<nblk, 256, fsmem, ex.stream>>>(V, tau, w, nref, Tw);
     const size_t asmem = wy_apply_smem<T>(w);
     if (asmem > 48 * 1024) allow_dynamic_smem(reinterpret_cast<const void*>(wy_apply_kernel<T>), asmem);
-    wy_apply_kernel<T><<<(m + WY_WARPS - 1) / WY_WARPS, WY_WARPS * 32, asmem, ex.stream>>>(X, ldx, w, m, nref, V,
-                                                                                           Tw, Vt, ldv);
+    wy_apply_kernel<T><<<(m + WY_WARPS - 1) / WY_WARPS, WY_WARPS * 32, asmem, ex.stream>>>(
+        X, ldx, w, m, nref, V, Tw, Vt, ldv, wy_slots<T>(w), ex.status);
     ex.launches += 2;
     return true;
 }
