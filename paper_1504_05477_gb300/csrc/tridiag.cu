@@ -18,6 +18,7 @@
 
 #include <cfloat>
 
+#include "chol_small.cuh"
 #include "common.cuh"
 #include "tc_common.cuh"
 
@@ -269,24 +270,30 @@ __global__ void __launch_bounds__(TD_NT) tridiag_kernel(const T* __restrict__ M,
     cl.sync();   // no CTA leaves while another may still read its shared memory
 }
 
-// Number of eigenvalues of T below x (Sturm sequence of the LDL^T pivots).
+// Numbers of eigenvalues of T below x0 and below x1 (Sturm sequences of the LDL^T
+// pivots), the two recurrences interleaved so that each hides the other's latency.
 template <typename T>
-__device__ int sturm_count(const T* d, const T* e2, int w, T x, T pivmin) {
-    int cnt = 0;
-    T q = d[0] - x;
-    if (fabs(q) < pivmin) q = -pivmin;
-    cnt += q < T(0);
+__device__ void sturm_count2(const T* d, const T* e2, int w, T x0, T x1, T pivmin, int& c0, int& c1) {
+    T q0 = d[0] - x0, q1 = d[0] - x1;
+    if (fabs(q0) < pivmin) q0 = -pivmin;
+    if (fabs(q1) < pivmin) q1 = -pivmin;
+    c0 = q0 < T(0);
+    c1 = q1 < T(0);
     for (int i = 1; i < w; ++i) {
-        q = (d[i] - x) - fast_div(e2[i - 1], q);
-        if (fabs(q) < pivmin) q = -pivmin;
-        cnt += q < T(0);
+        const T di = d[i], ei = e2[i - 1];
+        q0 = (di - x0) - fast_div(ei, q0);
+        q1 = (di - x1) - fast_div(ei, q1);
+        if (fabs(q0) < pivmin) q0 = -pivmin;
+        if (fabs(q1) < pivmin) q1 = -pivmin;
+        c0 += q0 < T(0);
+        c1 += q1 < T(0);
     }
-    return cnt;
 }
 
-// Eigenvalue i (descending, i < m) of T per warp: Gershgorin interval, then rounds of 31
-// Sturm counts keeping the 1/32 of the interval that holds it, to an absolute width of
-// 4 eps |T|.  lam[i] = midpoint; block 0 also stores |T| (largest Gershgorin bound).
+// Eigenvalue i (descending, i < m) of T per warp: Gershgorin interval, then rounds of 63
+// Sturm counts (two per lane) keeping the 1/64 of the interval that holds it, to an
+// absolute width of 4 eps |T|.  lam[i] = midpoint; block 0 also stores |T| (largest
+// Gershgorin bound).
 template <typename T>
 __global__ void bisect_kernel(const T* __restrict__ dT, const T* __restrict__ eT, int w, int m,
                               T* __restrict__ lam, T* __restrict__ tn) {
@@ -332,14 +339,21 @@ __global__ void bisect_kernel(const T* __restrict__ dT, const T* __restrict__ eT
     const int t = w - 1 - i;   // ascending index
     const T tol = T(4) * eps * tnorm + pivmin;
     T a = lo, b = hi;
+    // shift k < 64: a + (b - a) (k + 1) / 64 (k = 63: b, counted as w); lane l holds
+    // k = 2l and 2l + 1, and the first shift with more than t eigenvalues below it is the
+    // earlier of the first even and the first odd one the two ballots find.
+    auto shift = [&](int k) -> T { return k == 63 ? b : a + (b - a) * (T(k + 1) / T(64)); };
     for (int it = 0; it < 16 && b - a > tol; ++it) {
-        const T x = lane == 31 ? b : a + (b - a) * (T(lane + 1) / T(32));
-        const int cnt = lane == 31 ? w : sturm_count(d, e2, w, x, pivmin);
-        const unsigned mask = __ballot_sync(0xffffffffu, cnt >= t + 1);
-        const int ls = __ffs(mask) - 1;   // first shift with more than t eigenvalues below
-        const T xa = __shfl_sync(0xffffffffu, x, ls > 0 ? ls - 1 : 0);
-        const T xb = __shfl_sync(0xffffffffu, x, ls);
-        if (ls > 0) a = xa;
+        const T x0 = shift(2 * lane), x1 = shift(2 * lane + 1);
+        int c0, c1;
+        sturm_count2(d, e2, w, x0, x1, pivmin, c0, c1);
+        if (lane == 31) c1 = w;
+        const unsigned m0 = __ballot_sync(0xffffffffu, c0 >= t + 1);
+        const unsigned m1 = __ballot_sync(0xffffffffu, c1 >= t + 1);
+        const int l0 = m0 ? __ffs(m0) - 1 : 32, l1 = __ffs(m1) - 1;
+        const int ks = min(2 * l0, 2 * l1 + 1);   // first shift with more than t below
+        const T xa = shift(ks > 0 ? ks - 1 : 0), xb = shift(ks);
+        if (ks > 0) a = xa;
         b = xb;
     }
     if (lane == 0) lam[i] = T(0.5) * (a + b);
@@ -556,13 +570,13 @@ __global__ void __launch_bounds__(WY_WARPS * 32) wy_apply_kernel(const T* __rest
                                                                  int m, int nref, const T* __restrict__ V,
                                                                  const T* __restrict__ Tw, T* __restrict__ Vt,
                                                                  int64_t ldv, int ns, int* __restrict__ status) {
-    extern __shared__ __align__(128) unsigned char wy_smem[];
+    extern __shared__ __align__(16) unsigned char wya_smem[];
     __shared__ uint64_t full[WY_MAXS];
     __shared__ int abort_flag;
     const int64_t vp = v_pitch(w);
     const int64_t slot = WY_NB * vp + WY_NB * WY_NB;          // elements per ring slot
     const uint32_t vbytes = uint32_t(WY_NB * vp * sizeof(T)), tbytes = uint32_t(WY_NB * WY_NB * sizeof(T));
-    T* ring = reinterpret_cast<T*>(wy_smem);
+    T* ring = reinterpret_cast<T*>(wya_smem);
     T* xs = ring + ns * slot;                                 // WY_WARPS x vp
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int t = blockIdx.x * WY_WARPS + warp;
@@ -652,6 +666,117 @@ template <typename T>
 size_t wy_apply_smem(int w) {
     const size_t vp = size_t(v_pitch(w));
     return (size_t(wy_slots<T>(w)) * (WY_NB * vp + WY_NB * WY_NB) + WY_WARPS * vp) * sizeof(T);
+}
+
+// CholeskyQR2 of a small FP32 block held whole in one CTA's shared memory: X (c x ld,
+// rows = vectors of length len), c <= 64, in place.  Each pass forms the Gram
+// G = X X^T (4 x 4 tiles, one warp per tile with the lanes splitting the length, so
+// every entry sums len / 32 products per lane and then a 32-way tree), factors
+// G = L L^T into P = L^{-1} (chol_inv_block: shifted retries and breakdown flagged in
+// status) and applies X <- P X, one thread per column of X.
+constexpr int SQ_NT = 512;
+constexpr int SQ_C = 64;
+constexpr int SQ_GP = 65;   // row pitch of G
+constexpr int SQ_PP = 68;   // row pitch of P (float4 rows)
+inline int64_t sq_pitch(int len) { return (int64_t(len) + 3) / 4 * 4; }
+inline size_t sq_smem(int c, int len) {
+    return (size_t((c + 3) / 4 * 4) * size_t(sq_pitch(len)) + size_t(SQ_C) * (SQ_GP + SQ_PP)) * sizeof(float);
+}
+
+__global__ void __launch_bounds__(SQ_NT) small_cholqr2_kernel(float* __restrict__ X, int c, int len, int64_t ld,
+                                                              int* __restrict__ status, int* __restrict__ shifted) {
+    extern __shared__ __align__(16) unsigned char sq_smem_raw[];
+    const int64_t xp = (int64_t(len) + 3) / 4 * 4;
+    const int c4 = (c + 3) / 4 * 4;
+    float* Xs = reinterpret_cast<float*>(sq_smem_raw);   // c4 x xp
+    float* G = Xs + c4 * xp;                              // SQ_C x SQ_GP
+    float* P = G + SQ_C * SQ_GP;                          // SQ_C x SQ_PP
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int e = tid; e < c4 * len; e += SQ_NT) {
+        const int a = e / len, i = e - a * len;
+        Xs[a * xp + i] = a < c ? X[int64_t(a) * ld + i] : 0.f;
+    }
+    __syncthreads();
+    const int nt = c4 / 4, ntiles = nt * (nt + 1) / 2;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int e = warp; e < ntiles; e += SQ_NT / 32) {
+            int ta = 0, rem = e;   // tile (ta, tb), ta <= tb, row-major over the upper triangle
+            while (rem >= nt - ta) {
+                rem -= nt - ta;
+                ++ta;
+            }
+            const int tb = ta + rem;
+            float acc[4][4] = {};
+            for (int i = lane; i < len; i += 32) {
+                float xa[4], xb[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    xa[r] = Xs[(4 * ta + r) * xp + i];
+                    xb[r] = Xs[(4 * tb + r) * xp + i];
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(xa[r], xb[q], acc[r][q]);
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[r][q] = warp_sum(acc[r][q]);
+            if (lane == 0)
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int a = 4 * ta + r, b = 4 * tb + q;
+                        if (a < c && b < c) {
+                            G[a * SQ_GP + b] = acc[r][q];
+                            G[b * SQ_GP + a] = acc[r][q];
+                        }
+                    }
+        }
+        __syncthreads();
+        chol_inv_block(G, SQ_GP, c, P, SQ_PP, status, shifted);
+        __syncthreads();
+        for (int i = tid; i < len; i += SQ_NT) {
+            float x[SQ_C];
+#pragma unroll
+            for (int b = 0; b < SQ_C; ++b) x[b] = b < c ? Xs[b * xp + i] : 0.f;
+#pragma unroll
+            for (int a = 0; a < SQ_C; ++a) {
+                if (a >= c) break;
+                float y = 0.f;
+#pragma unroll
+                for (int b4 = 0; b4 <= a; b4 += 4) {   // P is lower triangular: P[a][b] = 0 for b > a
+                    const float4 pr = *reinterpret_cast<const float4*>(P + a * SQ_PP + b4);
+                    y = fmaf(pr.x, x[b4], y);
+                    if (b4 + 1 <= a) y = fmaf(pr.y, x[b4 + 1], y);
+                    if (b4 + 2 <= a) y = fmaf(pr.z, x[b4 + 2], y);
+                    if (b4 + 3 <= a) y = fmaf(pr.w, x[b4 + 3], y);
+                }
+                Xs[a * xp + i] = y;
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < c * len; e += SQ_NT) {
+        const int a = e / len, i = e - a * len;
+        X[int64_t(a) * ld + i] = Xs[a * xp + i];
+    }
+}
+
+// The small-block CholeskyQR2 above when it applies (FP32, c <= 64, the block within the
+// shared-memory budget); false: the caller orthonormalises through orth_block.
+bool small_cholqr2(Exec& ex, float* X, int c, int len, int64_t ld, int* shifted_flag) {
+    if (shifted_flag == nullptr || c < 1 || c > SQ_C || len < c || sq_smem(c, len) > SMEM_MAX) return false;
+    const size_t smem = sq_smem(c, len);
+    if (allow_dynamic_smem(reinterpret_cast<const void*>(small_cholqr2_kernel), smem) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    small_cholqr2_kernel<<<1, SQ_NT, smem, ex.stream>>>(X, c, len, ld, ex.status, shifted_flag);
+    ex.launches += 1;
+    return true;
 }
 
 }  // namespace
@@ -754,8 +879,10 @@ bool topk_tridiag(Exec& ex, int w, const T* M, int m, T* Vt, int64_t ldv, T* scr
     ex.launches += 1;
     // orthonormal eigenvector basis (CholeskyQR2 of the m x w block; thin blocks keep
     // their pad rows at zero, so the scratch block starts zeroed)
-    cudaMemsetAsync(Xtmp, 0, size_t(m) * ldx * sizeof(T), ex.stream);
-    orth_block<T>(ex, w, ldx, X, 0, X, m, Xtmp, X, ows);
+    if (!(sizeof(T) == 4 && small_cholqr2(ex, reinterpret_cast<float*>(X), m, w, ldx, ows.shifted_flag))) {
+        cudaMemsetAsync(Xtmp, 0, size_t(m) * ldx * sizeof(T), ex.stream);
+        orth_block<T>(ex, w, ldx, X, 0, X, m, Xtmp, X, ows);
+    }
     const int nref = w - 2;
     const int nblk = (nref + WY_NB - 1) / WY_NB;
     const size_t fsmem = size_t(WY_NB) * v_pitch(w) * sizeof(T);
