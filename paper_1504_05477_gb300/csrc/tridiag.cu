@@ -185,17 +185,22 @@ __global__ void __launch_bounds__(TD_NT) tridiag_kernel(const T* __restrict__ M,
         }
         if (act) {
             // p_c = tau (A(j+1, c) + scal sum_{i >= j+2} A(i, c) x_i)
-            T s0 = T(0), s1 = T(0);
+            // four rows per pass, all eight loads issued before the products
+            T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
             const T* col = A + lt * wp;
             if (colv && ct > j) {
                 int i = j + 2 + sub;
-                for (; i + tpc < w; i += 2 * tpc) {
-                    s0 += col[i] * xa[i];
-                    s1 += col[i + tpc] * xa[i + tpc];
+                for (; i + 3 * tpc < w; i += 4 * tpc) {
+                    const T a0 = col[i], a1 = col[i + tpc], a2 = col[i + 2 * tpc], a3 = col[i + 3 * tpc];
+                    const T x0 = xa[i], x1 = xa[i + tpc], x2 = xa[i + 2 * tpc], x3 = xa[i + 3 * tpc];
+                    s0 += a0 * x0;
+                    s1 += a1 * x1;
+                    s2 += a2 * x2;
+                    s3 += a3 * x3;
                 }
-                if (i < w) s0 += col[i] * xa[i];
+                for (; i < w; i += tpc) s0 += col[i] * xa[i];
             }
-            T s = s0 + s1;
+            T s = (s0 + s1) + (s2 + s3);
             for (int o = tpc >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             T dp = T(0);
             if (colv && ct > j && sub == 0) {
@@ -248,7 +253,22 @@ __global__ void __launch_bounds__(TD_NT) tridiag_kernel(const T* __restrict__ M,
             if (colv && ct > j + 1) {
                 const T vc = xa[ct] * scal, wc = pv[ct] - K * vc;
                 T* col = A + lt * wp;
-                for (int i = j + 2 + sub; i < w; i += tpc) {
+                int i = j + 2 + sub;
+                for (; i + 3 * tpc < w; i += 4 * tpc) {   // four rows per pass, loads first
+                    T c4[4], x4[4], p4[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        c4[u] = col[i + u * tpc];
+                        x4[u] = xa[i + u * tpc];
+                        p4[u] = pv[i + u * tpc];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const T vi = x4[u] * scal;
+                        col[i + u * tpc] = c4[u] - (vi * wc + (p4[u] - K * vi) * vc);
+                    }
+                }
+                for (; i < w; i += tpc) {
                     const T vi = xa[i] * scal;
                     col[i] -= vi * wc + (pv[i] - K * vi) * vc;
                 }
