@@ -3,8 +3,11 @@
 // Gram-Schmidt twice (BCGS2), then CholeskyQR twice, the second pass reduced to a
 // symmetric correction when the first one left the block orthonormal to rounding level:
 //   P1  C1 = Q^T W
-//   P2  W' = W - Q C1;   C2 = Q^T W'
+//   P2  W' = W - Q C1;   C2 = Q^T W' and G' = W'^T W' (one cross-CTA reduction)
 //   P3  W'' = W' - Q C2;   H2 = W''^T W'' = R1^T R1;   W1 = W'' R1^{-1}
+//       (H2 = G' - C2^T C2 by Pythagoras with Q^T Q = I; taken as G' when C2 is only
+//       the first projection's rounding error, else summed from W'' in a reduction of
+//       its own)
 //   P4  H3 = W1^T W1 = I + E;   Qout = W1 (I - E / 2) when ||E||_F^2 <= 1e-7 (then
 //       Qout^T Qout = I - (3/4) E^2 + O(E^3)), else Qout = W1 chol(H3)^{-1}
 // with every contraction on tcgen05 (kind::tf32) in three TF32 terms: for operands x, y
@@ -52,6 +55,12 @@ constexpr float MORE_PROJ = 10.f;
 // ||W1^T W1 - I||_F^2 up to which the second pass is the symmetric correction I - E / 2
 // (its error (3/4) ||E||^2 then stays below 1e-7)
 constexpr float NEWTON_E2 = 1e-7f;
+// The second projection's coefficients C2 = Q^T W' and the Gram G' = W'^T W' are summed in
+// one cross-CTA reduction, and H2 = W''^T W'' = G' - C2^T C2 is taken as G', when the first
+// projection removed at most this many times the energy it left: C2 is then the first
+// pass's rounding error, and C2^T C2 is far below G' (the second CholeskyQR pass corrects
+// what is left)
+constexpr float MERGE_RATIO = 1e4f;
 
 __host__ __device__ constexpr int r16(int x) { return (x + 15) & ~15; }
 __host__ __device__ constexpr int r4(int x) { return (x + 3) & ~3; }
@@ -338,13 +347,13 @@ __device__ __forceinline__ bool gram_w(Kst& k) {
 
 // Gram epilogues: lanes j < c of the accumulator -> this CTA's partial part[cta][r][j]
 // (r < m: the Q Gram of gram_q; r < c: the windows of gram_w, summed in FP32)
-__device__ __forceinline__ void gram_out(Kst& k, bool windowed) {
+__device__ __forceinline__ void gram_out(Kst& k, bool windowed, int roff = 0) {
     const int cols = windowed ? 64 : k.m16;
     const int R = windowed ? k.c : k.m;
     const int ngroups = (cols + 31) / 32;
     if (k.warp == 0 || k.warp == 1 || k.warp == 4 || k.warp == 5) {
         const int j = (k.warp & 1) * 32 + k.lane;
-        float* dst = k.a->part + int64_t(k.cta) * k.a->prow * k.a->cpad + j;
+        float* dst = k.a->part + (int64_t(k.cta) * k.a->prow + roff) * k.a->cpad + j;
         for (int g = (k.warp >> 2); g < ngroups; g += 2) {
             float v[32];
             tmem_ld32(k.tmem + k.lanes + uint32_t(g * 32), v);
@@ -369,21 +378,24 @@ __device__ __forceinline__ void gram_out(Kst& k, bool windowed) {
     __syncthreads();
 }
 
-// Ordered cross-CTA sum of the partials (R rows): with_q, the coefficients go to the C
-// tiles (global, hi / lo, read back by TMA); otherwise the c x c Gram goes to hbuf
-__device__ __forceinline__ bool reduce(Kst& k, int R, bool with_q) {
+// Ordered cross-CTA sum of the partials (R rows): rows r < qrows are coefficients and go
+// to the C tiles (global, hi / lo, read back by TMA); the next c rows are a c x c Gram and
+// go to hbuf, the row after them (the projection energies) to hbuf row c
+__device__ __forceinline__ bool reduce(Kst& k, int R, int qrows) {
+    const bool with_q = qrows > 0;
     const Args& a = *k.a;
     __threadfence();
     if (!grid_sync(k.ctl, a.bar, ++k.phase * unsigned(k.G), a.status)) return false;
     const int c = k.c;
     reduce_stripe(a.part, k.G, int64_t(a.prow) * a.cpad, R * a.cpad, a.cpad, k.red, [&](int j, int r, float v) {
         if (j >= c) return;
-        if (with_q) {
+        if (r < qrows) {
             const float h = hi_of(v);
             a.cts[int64_t(j) * a.ldct + r] = h;
             a.cts[int64_t(64 + j) * a.ldct + r] = v - h;
         } else {
-            a.hbuf[r < c ? j * c + r : c * c + j] = v;   // row c: the energies ||C_j||^2
+            const int g = r - qrows;
+            a.hbuf[g < c ? j * c + g : c * c + j] = v;   // row c: the energies ||C_j||^2
         }
     });
     if (with_q) asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -449,7 +461,7 @@ __device__ __forceinline__ bool update_pass(Kst& k) {
 // epilogue of an update pass: W[j][l] -= D[j][l] in the W tiles.  This CTA's share of
 // ||D_j||^2 (= ||Q C_j||^2 = ||C_j||^2, the energy the projection removed) goes to row c
 // of its partial, which the next reduction of a c x c Gram sums with it.
-__device__ __forceinline__ void update_out(Kst& k) {
+__device__ __forceinline__ void update_out(Kst& k, int erow) {
     const int ngroups = (k.S16 + 31) / 32;
     if (k.warp == 0 || k.warp == 1 || k.warp == 4 || k.warp == 5) {
         const int j = (k.warp & 1) * 32 + k.lane;
@@ -471,7 +483,7 @@ __device__ __forceinline__ void update_out(Kst& k) {
         if (k.warp >= 4) rr[j] = e2;
         named_sync(2, 128);
         if (k.warp < 4 && j < k.c)
-            k.a->part[(int64_t(k.cta) * k.a->prow + k.c) * k.a->cpad + j] = e2 + rr[j];
+            k.a->part[(int64_t(k.cta) * k.a->prow + erow) * k.a->cpad + j] = e2 + rr[j];
     }
     fence_async_smem();
     tc_fence_before();
@@ -497,6 +509,21 @@ __device__ __forceinline__ bool more_projection(Kst& k) {
     }
     __syncthreads();
     return k.ctl->bad != 0;
+}
+
+// H2 = G' for the merged second projection?  The energy the first projection removed
+// (row c of hbuf) against trace(G') = ||W'||_F^2; the same in every CTA
+__device__ __forceinline__ bool merge_holds(Kst& k) {
+    if (k.tid == 0) {
+        float cn = 0.f, tr = 0.f;
+        for (int j = 0; j < k.c; ++j) {
+            cn += __ldcg(k.a->hbuf + k.c * k.c + j);
+            tr += k.gbuf[j * GP + j];
+        }
+        k.ctl->bad = (cn <= MERGE_RATIO * tr) ? 0 : 1;   // NaN: not merged
+    }
+    __syncthreads();
+    return k.ctl->bad == 0;
 }
 
 // pbuf = R^{-T} for gbuf = R^T R (shifted retries and breakdown as chol_inv_block_t)
@@ -688,33 +715,49 @@ __global__ void __launch_bounds__(NT, 1)
     k.lanes = uint32_t((k.warp & 3) * 32) << 16;   // this warp's TMEM lane quarter
     bool ok = true;
 
-    // P1, P2: two projections, C = Q^T W then W -= Q C
-    for (int pass = 0; pass < 2 && ok && m > 0; ++pass) {
+    // P1: C1 = Q^T W, W' = W - Q C1 (the energy it removed to partial row m + c)
+    // P2: C2 = Q^T W' and G' = W'^T W' in one reduction, W'' = W' - Q C2; H2 = G' when
+    //     merge_holds, else (P3) H2 = W''^T W'' in a reduction of its own
+    bool merged = false;
+    if (m > 0) {
         ok = gram_q(k);
         if (ok) gram_out(k, false);
-        if (ok) ok = reduce(k, m, true);
+        if (ok) ok = reduce(k, m, m);
         if (ok) ok = update_pass(k);
-        if (ok) update_out(k);
+        if (ok) update_out(k, m + c);
+        if (ok) ok = gram_q(k);
+        if (ok) gram_out(k, false);
+        if (ok) ok = gram_w(k);
+        if (ok) gram_out(k, true, m);
+        if (ok) ok = reduce(k, m + c + 1, m);
+        if (ok) ok = update_pass(k);
+        if (ok) update_out(k, c);
+        if (ok) {   // after the update: its stages share shared memory with gbuf
+            load_h(k);
+            merged = merge_holds(k);
+        }
     }
     // P3: H2 = W''^T W''; then R1^T R1 = H2, W1 = W'' R1^{-1}
-    if (ok) ok = gram_w(k);
-    if (ok) gram_out(k, true);
-    if (ok) ok = reduce(k, m > 0 ? c + 1 : c, false);
-    if (ok) load_h(k);
+    if (ok && !merged) {
+        ok = gram_w(k);
+        if (ok) gram_out(k, true);
+        if (ok) ok = reduce(k, m > 0 ? c + 1 : c, 0);
+        if (ok) load_h(k);
+    }
     // The tensor cores' truncating accumulation makes the error of Q C roughly
     // proportional to Q C, i.e. it lies inside span(Q).  When the block was almost
     // entirely inside span(Q) (the second projection removed much more energy than it
     // left: a converged or rank-deficient Krylov direction), that error is not small
     // against what is left, and one more projection removes it (at most two more).
-    for (int extra = 0; extra < 2 && ok && m > 0 && more_projection(k); ++extra) {
+    for (int extra = 0; extra < 2 && ok && m > 0 && !merged && more_projection(k); ++extra) {
         ok = gram_q(k);
         if (ok) gram_out(k, false);
-        if (ok) ok = reduce(k, m, true);
+        if (ok) ok = reduce(k, m, m);
         if (ok) ok = update_pass(k);
-        if (ok) update_out(k);
+        if (ok) update_out(k, c);
         if (ok) ok = gram_w(k);
         if (ok) gram_out(k, true);
-        if (ok) ok = reduce(k, c + 1, false);
+        if (ok) ok = reduce(k, c + 1, 0);
         if (ok) load_h(k);
     }
     if (ok) {
@@ -727,7 +770,7 @@ __global__ void __launch_bounds__(NT, 1)
     // P4: H3 = W1^T W1, Qout = W1 (I - E / 2) or W1 chol(H3)^{-1}
     if (ok) ok = gram_w(k);
     if (ok) gram_out(k, true);
-    if (ok) ok = reduce(k, c, false);
+    if (ok) ok = reduce(k, c, 0);
     if (ok) {
         load_h(k);
         second_factor(k);
